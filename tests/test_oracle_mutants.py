@@ -1,0 +1,93 @@
+"""The pins are strong enough: plant plausible mistakes in a copy of the
+oracle's C source (CPU only) and check that every one of them makes at least
+one pin fail.  The real oracle is untouched.
+"""
+import json
+import os
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as pins
+from oracle import oracle as O
+
+# (name, original text, planted mistake); each original must occur exactly once.
+MUTANTS = [
+    ("extend uses open (score)", "E = max2(E - e, Hleft - o);", "E = max2(E - o, Hleft - o);"),
+    ("F sign error (score)", "int64_t F = max2(Frow[j] - e, Hup - o);",
+     "int64_t F = max2(Frow[j] + e, Hup - o);"),
+    ("transposed matrix (score)", "int64_t H = Hdiag + S[a[i - 1] * K + b[j - 1]];",
+     "int64_t H = Hdiag + S[b[j - 1] * K + a[i - 1]];"),
+    ("dropped zero floor (score)", "            H = max2(H, 0);\n            Frow[j] = F;",
+     "            Frow[j] = F;"),
+    ("row-major end tie-break", "    if (j != bj) return j < bj;\n    return i < bi;",
+     "    if (i != bi) return i < bi;\n    return j < bj;"),
+    ("wrong diagonal index (full)", "int64_t h = AT(H, i - 1, j - 1) + S[a[i - 1] * K + b[j - 1]];",
+     "int64_t h = AT(H, i - 1, j) + S[a[i - 1] * K + b[j - 1]];"),
+    ("E opens with extend (full traceback)", "if (AT(E, i, j) == AT(H, i, j - 1) - o) state = 0;",
+     "if (AT(E, i, j) == AT(H, i, j - 1) - e) state = 0;"),
+    ("F before E (full traceback)",
+     "                } else if (h == AT(E, i, j)) {\n                    state = 1;\n"
+     "                } else {\n                    state = 2;",
+     "                } else if (h == AT(F, i, j)) {\n                    state = 2;\n"
+     "                } else {\n                    state = 1;"),
+    ("extend before open (ptr)", "if (Fcur == f_open) p |= 8;", "if (Fcur == f_ext) p |= 8;"),
+    ("E source mislabelled (ptr)", "else if (h == Ecur) src = 2;", "else if (h == Fcur) src = 2;"),
+    ("no stop at zero (full)", "                if (h == 0) break;\n", "                if (i == 0 || j == 0) break;\n"),
+]
+
+
+def _battery(lib):
+    """Run the quick pins against one compiled copy; return the names that failed."""
+    failed = []
+    checks = [
+        ("bruteforce", lambda: pins.test_bruteforce_random_small(lib, 4)),
+        ("bruteforce-gappy", lambda: pins.test_bruteforce_gappy_scoring(lib)),
+        ("exhaustive", lambda: pins.test_bruteforce_exhaustive_binary(lib)),
+        ("symmetry", lambda: pins.test_symmetry(lib)),
+        ("linear", lambda: pins.test_open_equals_extend_is_linear_gap(lib)),
+        ("kadane", lambda: pins.test_huge_gaps_is_kadane(lib)),
+        ("self-dna", lambda: pins.test_self_alignment_dna_closed_form(lib)),
+        ("rescoring", lambda: pins.test_rescoring_medium_cases(lib)),
+    ]
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:  # noqa: BLE001 - any failure counts as caught
+            failed.append(name)
+    return failed
+
+
+def test_unmutated_copy_passes_battery():
+    with tempfile.TemporaryDirectory() as d:
+        so = O.compile_source(O.SOURCE, os.path.join(d, "copy.so"))
+        assert _battery(O.OracleLib(so)) == []
+
+
+def _battery_in_child(so_path):
+    """Run the battery in a fresh interpreter: a planted mistake may crash it,
+    which counts as caught."""
+    code = ("import json, sys; sys.path[:0] = %r; import test_oracle_mutants as T; "
+            "from oracle import oracle as O; print(json.dumps(T._battery(O.OracleLib(%r))))"
+            % ([os.path.dirname(os.path.abspath(__file__)),
+                os.path.dirname(os.path.dirname(os.path.abspath(__file__)))], so_path))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return ["crashed (%d)" % r.returncode]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+@pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, orig, bad):
+    src = open(O.SOURCE).read()
+    assert src.count(orig) == 1, name
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mutant.c")
+        with open(c, "w") as f:
+            f.write(src.replace(orig, bad))
+        so = O.compile_source(c, os.path.join(d, "mutant.so"))
+        failed = _battery_in_child(so)
+    assert failed, "planted mistake %r was not caught by any pin" % name

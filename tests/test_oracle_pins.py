@@ -1,0 +1,225 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+* brute-force enumeration of every local alignment (|a|, |b| <= 7): score,
+  canonical end cell and canonical traceback;
+* closed forms: DNA and protein self-alignment;
+* score symmetry under swapping the sequences (with the transposed matrix);
+* open == extend against an independent linear-gap Smith-Waterman;
+* prohibitive gap penalties against Kadane's maximum subarray on diagonals;
+* rescoring of every emitted CIGAR by a separate scorer;
+* BLOSUM62 table invariants.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from bruteforce import brute_force, rescore
+from paper_2211_10769_gb300 import workloads as W
+
+
+def _rand_case(g, K, Lmax, strict_gap=False):
+    m = int(g.integers(0, Lmax + 1))
+    n = int(g.integers(0, Lmax + 1))
+    a = g.integers(0, K, size=m).astype(np.uint8)
+    b = g.integers(0, K, size=n).astype(np.uint8)
+    S = g.integers(-4, 7, size=(K, K)).astype(np.int8)
+    o = int(g.integers(0, 7))
+    e = int(g.integers(0, o + 1))
+    if strict_gap and e == o:
+        o += 1
+    return a, b, S, o, e
+
+
+def _check_against_brute(oracle_mod, a, b, S, o, e, check_path):
+    score, i_end, j_end, canon = brute_force(a, b, S, o, e)
+    assert oracle_mod.sw_score(a, b, S, o, e) == (score, i_end, j_end)
+    for aln in (oracle_mod.sw_align(a, b, S, o, e), oracle_mod.sw_align_ptr(a, b, S, o, e)):
+        assert (aln.score, aln.a_end, aln.b_end) == (score, i_end, j_end)
+        if score == 0:
+            assert aln.cigar == "" and (aln.a_begin, aln.b_begin) == (0, 0)
+            continue
+        assert rescore(a, b, S, o, e, aln.a_begin, aln.b_begin, aln.cigar) == (score, i_end, j_end)
+        if check_path:
+            ops = oracle_mod.cigar_from_ops(canon[2])
+            assert (aln.a_begin, aln.b_begin, aln.cigar) == (canon[0], canon[1], ops)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_bruteforce_random_small(oracle_mod, K):
+    g = np.random.default_rng(W.BASE_SEED + 7 + K)
+    for _ in range(150):
+        a, b, S, o, e = _rand_case(g, K, 6)
+        _check_against_brute(oracle_mod, a, b, S, o, e, check_path=(e < o))
+
+
+def test_bruteforce_length7(oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 77)
+    for _ in range(12):
+        a, b, S, o, e = _rand_case(g, 4, 7, strict_gap=True)
+        a = g.integers(0, 4, size=7).astype(np.uint8)
+        b = g.integers(0, 4, size=7).astype(np.uint8)
+        _check_against_brute(oracle_mod, a, b, S, o, e, check_path=True)
+
+
+def test_bruteforce_gappy_scoring(oracle_mod):
+    """Large match reward and cheap gaps, so that optimal alignments carry gaps."""
+    g = np.random.default_rng(W.BASE_SEED + 78)
+    S = np.full((4, 4), -3, dtype=np.int8)
+    np.fill_diagonal(S, 6)
+    seen_gap = False
+    for _ in range(60):
+        m, n = int(g.integers(3, 7)), int(g.integers(3, 7))
+        a = g.integers(0, 4, size=m).astype(np.uint8)
+        b = g.integers(0, 4, size=n).astype(np.uint8)
+        o = int(g.integers(1, 4))
+        e = int(g.integers(0, o))
+        _check_against_brute(oracle_mod, a, b, S, o, e, check_path=True)
+        aln = oracle_mod.sw_align(a, b, S, o, e)
+        seen_gap |= ("I" in aln.cigar) or ("D" in aln.cigar)
+    assert seen_gap
+
+
+def test_bruteforce_exhaustive_binary(oracle_mod):
+    """Every pair of binary strings of length <= 4 under two scorings."""
+    seqs = [np.array(s, dtype=np.uint8) for L in range(5) for s in itertools.product([0, 1], repeat=L)]
+    S1 = np.array([[2, -1], [-1, 3]], dtype=np.int8)
+    S2 = np.array([[5, -4], [-2, 4]], dtype=np.int8)     # not symmetric on purpose
+    for S, o, e in ((S1, 2, 1), (S2, 3, 0), (S1, 1, 1)):
+        for a in seqs:
+            for b in seqs:
+                _check_against_brute(oracle_mod, a, b, S, o, e, check_path=(e < o))
+
+
+def test_self_alignment_dna_closed_form(oracle_mod):
+    sc = W.dna_scoring()
+    for L in (1, 17, 500, 2000):
+        a = W.uniform_dna(L, W.BASE_SEED + 900 + L)
+        aln = oracle_mod.sw_align(a, a, sc.matrix, sc.gap_open, sc.gap_extend)
+        assert aln.score == L
+        assert (aln.a_begin, aln.a_end, aln.b_begin, aln.b_end, aln.cigar) == (0, L, 0, L, "%dM" % L)
+
+
+def test_blosum62_invariants():
+    B = W.blosum62()
+    assert B.shape == (24, 24)
+    assert (B == B.T).all()
+    assert B.min() == -4 and B.max() == 11
+    assert B[W.PROTEIN_ALPHABET.index("W"), W.PROTEIN_ALPHABET.index("W")] == 11
+    d = np.diag(B)[:20]
+    assert (d > 0).all()
+    # S(x,y) <= (S(x,x) + S(y,y)) / 2 for the 20 standard letters, which is
+    # what makes self-alignment the sum of the diagonal.
+    for x in range(20):
+        for y in range(20):
+            if x != y:
+                assert 2 * int(B[x, y]) <= int(B[x, x]) + int(B[y, y])
+    # a few entries that are easy to misplace
+    P = W.PROTEIN_ALPHABET.index
+    assert B[P("C"), P("C")] == 9 and B[P("H"), P("H")] == 8 and B[P("P"), P("P")] == 7
+    assert B[P("I"), P("V")] == 3 and B[P("D"), P("E")] == 2 and B[P("*"), P("*")] == 1
+    assert B[P("B"), P("D")] == 4 and B[P("Z"), P("E")] == 4 and B[P("X"), P("X")] == -1
+
+
+def test_self_alignment_protein_closed_form(oracle_mod):
+    sc = W.protein_scoring()
+    B = sc.matrix
+    for L in (1, 50, 700):
+        a = W.random_protein(L, W.BASE_SEED + 950 + L)
+        aln = oracle_mod.sw_align(a, a, B, sc.gap_open, sc.gap_extend)
+        assert aln.score == int(sum(int(B[x, x]) for x in a))
+        assert aln.cigar == "%dM" % L
+
+
+def test_symmetry(oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 31)
+    for _ in range(40):
+        K = int(g.integers(2, 8))
+        m, n = int(g.integers(0, 60)), int(g.integers(0, 60))
+        a = g.integers(0, K, size=m).astype(np.uint8)
+        b = g.integers(0, K, size=n).astype(np.uint8)
+        S = g.integers(-5, 6, size=(K, K)).astype(np.int8)
+        o = int(g.integers(0, 8))
+        e = int(g.integers(0, o + 1))
+        s1 = oracle_mod.sw_score(a, b, S, o, e)[0]
+        s2 = oracle_mod.sw_score(b, a, np.ascontiguousarray(S.T), o, e)[0]
+        assert s1 == s2
+
+
+def _linear_gap_sw(a, b, S, g):
+    """Textbook one-matrix Smith-Waterman with linear gap cost g per gap letter."""
+    m, n = len(a), len(b)
+    prev = [0] * (n + 1)
+    best = 0
+    for i in range(1, m + 1):
+        cur = [0] * (n + 1)
+        for j in range(1, n + 1):
+            cur[j] = max(0, prev[j - 1] + int(S[a[i - 1]][b[j - 1]]), prev[j] - g, cur[j - 1] - g)
+            best = max(best, cur[j])
+        prev = cur
+    return best
+
+
+def test_open_equals_extend_is_linear_gap(oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 41)
+    for _ in range(30):
+        K = int(g.integers(2, 6))
+        m, n = int(g.integers(0, 80)), int(g.integers(0, 80))
+        a = g.integers(0, K, size=m).astype(np.uint8)
+        b = g.integers(0, K, size=n).astype(np.uint8)
+        S = g.integers(-3, 6, size=(K, K)).astype(np.int8)
+        gap = int(g.integers(0, 5))
+        assert oracle_mod.sw_score(a, b, S, gap, gap)[0] == _linear_gap_sw(a, b, S, gap)
+
+
+def _kadane_diagonals(a, b, S):
+    best = 0
+    m, n = len(a), len(b)
+    for d in range(-m + 1, n):
+        run = 0
+        for i in range(m):
+            j = i + d
+            if 0 <= j < n:
+                run = max(0, run + int(S[a[i]][b[j]]))
+                best = max(best, run)
+    return best
+
+
+def test_huge_gaps_is_kadane(oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 51)
+    for _ in range(30):
+        K = int(g.integers(2, 6))
+        m, n = int(g.integers(0, 70)), int(g.integers(0, 70))
+        a = g.integers(0, K, size=m).astype(np.uint8)
+        b = g.integers(0, K, size=n).astype(np.uint8)
+        S = g.integers(-4, 5, size=(K, K)).astype(np.int8)
+        assert oracle_mod.sw_score(a, b, S, 10_000, 10_000)[0] == _kadane_diagonals(a, b, S)
+
+
+def test_rescoring_medium_cases(oracle_mod):
+    """Larger random cases: both traceback forms agree and every CIGAR rescores."""
+    g = np.random.default_rng(W.BASE_SEED + 61)
+    dna, prot = W.dna_scoring(), W.protein_scoring()
+    for t in range(16):
+        if t % 2 == 0:
+            A = W.uniform_dna(int(g.integers(50, 400)), W.BASE_SEED + 2000 + t)
+            B = W.mutate(A, 4, W.BASE_SEED + 3000 + t, p_sub=0.1, p_indel=0.03)
+            sc = dna
+        else:
+            A = W.random_protein(int(g.integers(50, 300)), W.BASE_SEED + 2000 + t)
+            B = W.mutate(A, 20, W.BASE_SEED + 3000 + t, p_sub=0.3, p_indel=0.03)
+            sc = prot
+        full = oracle_mod.sw_align(A, B, sc.matrix, sc.gap_open, sc.gap_extend)
+        ptr = oracle_mod.sw_align_ptr(A, B, sc.matrix, sc.gap_open, sc.gap_extend)
+        assert full == ptr
+        assert full.score == oracle_mod.sw_score(A, B, sc.matrix, sc.gap_open, sc.gap_extend)[0]
+        assert rescore(A, B, sc.matrix, sc.gap_open, sc.gap_extend, full.a_begin, full.b_begin,
+                       full.cigar) == (full.score, full.a_end, full.b_end)
+
+
+def test_encode(oracle_mod):
+    assert list(oracle_mod.encode("ACGT", "ACGTacgt")) == [0, 1, 2, 3, 0, 1, 2, 3]
+    codes = oracle_mod.encode(W.PROTEIN_ALPHABET, "ARNDCQEGHILKMFPSTWYVBZX*")
+    assert list(codes) == list(range(24))
+    with pytest.raises(ValueError):
+        oracle_mod.encode("ACGT", "ACGN")
