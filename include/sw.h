@@ -1,0 +1,170 @@
+/*
+ * sw.h -- C ABI of the GB300 Smith-Waterman / Gotoh library (libswgb.so).
+ *
+ * The library computes optimal local alignments (Smith-Waterman, paper
+ * Section 2.1.2) with affine gap penalties (gap open / gap extension, paper
+ * Section 2.2; values used in the experiments, Section 3.2) on one NVIDIA
+ * GB300 GPU.  It offers the two uses the paper distinguishes in Section
+ * 2.1: pairwise alignment of two (long) sequences, where all threads work on
+ * one matrix (intra-task parallelism), and database search, where many
+ * matrices are computed at once (inter-task parallelism); plus the
+ * resolution (score) and reconstruction (alignment path) phases the paper
+ * describes for SW# in Section 2.2.
+ *
+ * Recurrence (the paper names the method without printing it; this is the
+ * textbook Gotoh form).  Sequence a (length m) indexes rows i, sequence b
+ * (length n) indexes columns j, S is the substitution matrix, o = gap_open,
+ * e = gap_extend, a gap of k letters costs o + (k-1)*e:
+ *
+ *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o)     gap in a, consumes b_j  (I)
+ *   F(i,j) = max(F(i-1,j) - e, H(i-1,j) - o)     gap in b, consumes a_i  (D)
+ *   H(i,j) = max(0, H(i-1,j-1) + S(a_i,b_j), E(i,j), F(i,j))
+ *   H(0,*) = H(*,0) = 0
+ *
+ * Canonical results (the paper is silent on ties):
+ *   - end cell: the maximum H; among equal maxima the smallest column (b_end)
+ *     and then the smallest row (a_end);
+ *   - traceback from the end cell: in H prefer the diagonal, then E, then F,
+ *     stop where H = 0; inside a gap leave it (open) before extending it;
+ *   - coordinates are 0-based, begin inclusive, end exclusive; score 0 means
+ *     an empty alignment with all coordinates 0;
+ *   - CIGAR is run-length M/I/D; D consumes a only, I consumes b only.
+ *
+ * Conventions for every call:
+ *   - returns SW_OK (0) or a negative SW_E* code; outputs are untouched on
+ *     error; no C++ exception crosses the ABI;
+ *   - residues are pre-encoded codes 0 .. alphabet-1 (see sw_encode);
+ *   - sequence pointers may be host or device memory (the library asks the
+ *     CUDA driver which); host data is copied to the device inside the call;
+ *   - input buffers are borrowed and not retained after the call returns,
+ *     except by sw_db_create, which copies the database;
+ *   - output structs are caller-owned host memory, except the CIGAR string
+ *     of sw_alignment, which the library allocates and sw_alignment_free
+ *     releases;
+ *   - calls on one context are serialised on its CUDA stream and return
+ *     after the stream work they issued is complete; a context must not be
+ *     used from two host threads at once.
+ */
+#ifndef SWGB_SW_H
+#define SWGB_SW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SW_OK        0
+#define SW_EINVAL   (-1)   /* bad argument: null pointer, negative length, code >= alphabet, bad penalties */
+#define SW_ENOMEM   (-2)   /* device or host allocation failed */
+#define SW_ECUDA    (-3)   /* a CUDA runtime call failed */
+#define SW_ETIMEOUT (-4)   /* a bounded device-side wait gave up (see sw_ctx_create) */
+#define SW_EAGAIN   (-5)   /* resource busy / result not ready yet (serving calls) */
+#define SW_ERANGE   (-6)   /* a size or score beyond the documented limits */
+
+/* Largest sequence length accepted by the pairwise calls. */
+#define SW_MAX_LEN  ((int64_t)2000000000)
+
+typedef struct sw_ctx sw_ctx;   /* device, stream, scratch memory, tuning state */
+typedef struct sw_db  sw_db;    /* device-resident, length-sorted protein database */
+
+/*
+ * Scoring scheme (paper Sections 2.2 and 3.2: a substitution matrix plus gap
+ * open and gap extension penalties).  matrix is alphabet x alphabet int8,
+ * row-major, matrix[x*alphabet + y] = score of residue x of a (rows) against
+ * residue y of b (columns); it is copied at call time.  Penalties are given
+ * as non-negative numbers that are subtracted; 0 <= gap_extend <= gap_open
+ * <= 1,000,000 (with gap_extend > gap_open the Gotoh recurrence would not
+ * score maximal gap runs as open + (k-1)*extend).  1 <= alphabet <= 32.
+ */
+typedef struct {
+    int32_t alphabet;
+    const int8_t *matrix;
+    int32_t gap_open;
+    int32_t gap_extend;
+} sw_scoring;
+
+/* Score and canonical end cell of one pair. */
+typedef struct {
+    int32_t score;
+    uint32_t flags;        /* reserved, 0 */
+    int64_t a_end;         /* exclusive end in a (rows) */
+    int64_t b_end;         /* exclusive end in b (columns) */
+} sw_hit;
+
+/* Canonical alignment of one pair; cigar is owned by the library. */
+typedef struct {
+    int32_t score;
+    uint32_t flags;        /* reserved, 0 */
+    int64_t a_begin, a_end;
+    int64_t b_begin, b_end;
+    char *cigar;           /* NUL-terminated, run-length M/I/D; "" for score 0 */
+    int64_t cigar_len;     /* strlen(cigar) */
+} sw_alignment;
+
+/* One database hit. */
+typedef struct {
+    int64_t subject;       /* index of the subject in the database */
+    int32_t score;
+    uint32_t flags;        /* reserved, 0 */
+} sw_dbhit;
+
+/*
+ * Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream) on which every call of this context
+ * runs.  Device-side waits between thread blocks are bounded; a wait that
+ * gives up makes the call fail with SW_ETIMEOUT and leaves the context
+ * usable.
+ */
+int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out);
+void sw_ctx_destroy(sw_ctx *ctx);
+
+/* Human-readable text for a status code (static storage). */
+const char *sw_strerror(int status);
+
+/*
+ * Encode residue letters (step "encode" of the path): codes[k] = index of
+ * toupper(text[k]) in `alphabet` (a NUL-terminated string of at most 32
+ * distinct upper-case ASCII letters or '*', e.g. "ACGT" or
+ * "ARNDCQEGHILKMFPSTWYVBZX*").  text and codes may be host or device
+ * memory, len >= 0.  A character outside the alphabet gives SW_EINVAL and
+ * leaves codes unspecified.
+ */
+int sw_encode(sw_ctx *ctx, const char *alphabet, const char *text, int64_t len, uint8_t *codes);
+
+/*
+ * Resolution phase for one pair (paper Section 2.2): best local score and
+ * its canonical end cell.  0 <= m, n <= SW_MAX_LEN; every code < alphabet.
+ * Scores must fit in int32 (|score| <= min(m,n) * max|S| < 2^31), else
+ * SW_ERANGE.
+ */
+int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+             const sw_scoring *sc, sw_hit *out);
+
+/*
+ * Resolution and reconstruction for one pair (paper Section 2.2): score,
+ * canonical alignment path and coordinates.  Same limits as sw_score.  The
+ * path is reconstructed from traceback bits recomputed on the device from
+ * checkpoint rows, so device memory stays far below the m*n matrix.
+ * *out is written only on success; release it with sw_alignment_free.
+ */
+int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+             const sw_scoring *sc, sw_alignment *out);
+
+/* Free the CIGAR of an alignment filled by sw_align (NULL-safe). */
+void sw_alignment_free(sw_alignment *aln);
+
+/*
+ * Number of kernels this context has launched since it was created
+ * (diagnostics: lets a caller count device launches per call).  Returns -1
+ * for a null context.
+ */
+int64_t sw_ctx_launches(const sw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_SW_H */

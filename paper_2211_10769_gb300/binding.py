@@ -1,0 +1,206 @@
+"""Thin Python binding of libswgb (include/sw.h): argument marshalling only.
+
+Every step of the alignment runs in the CUDA library; this module converts
+numpy arrays / torch tensors into pointers, calls the C entry points and
+turns their outputs into Python values.  It raises if the compiled library
+is missing -- there is no CPU fallback.
+
+Sequences may be numpy uint8 arrays (host memory; the library copies them to
+the device inside the call) or uint8 torch CUDA tensors (device memory).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libswgb.so")
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_EAGAIN, SW_ERANGE = 0, -1, -2, -3, -4, -5, -6
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, _strerror(status), status))
+        self.status = status
+
+
+class _Scoring(ctypes.Structure):
+    _fields_ = [("alphabet", ctypes.c_int32), ("matrix", ctypes.c_void_p),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class _Hit(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("a_end", ctypes.c_int64), ("b_end", ctypes.c_int64)]
+
+
+class _Alignment(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("a_begin", ctypes.c_int64), ("a_end", ctypes.c_int64),
+                ("b_begin", ctypes.c_int64), ("b_end", ctypes.c_int64),
+                ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libswgb.so (built by paper_2211_10769_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libswgb.so is not built (run `python -m paper_2211_10769_gb300.build`); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.sw_strerror.restype = ctypes.c_char_p
+    lib.sw_strerror.argtypes = [i32]
+    lib.sw_ctx_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+    lib.sw_ctx_destroy.argtypes = [vp]
+    lib.sw_ctx_destroy.restype = None
+    lib.sw_encode.argtypes = [vp, ctypes.c_char_p, vp, i64, vp]
+    lib.sw_score.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(_Scoring), ctypes.POINTER(_Hit)]
+    lib.sw_align.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(_Scoring), ctypes.POINTER(_Alignment)]
+    lib.sw_alignment_free.argtypes = [ctypes.POINTER(_Alignment)]
+    lib.sw_alignment_free.restype = None
+    lib.sw_ctx_launches.argtypes = [vp]
+    lib.sw_ctx_launches.restype = i64
+    _lib = lib
+    return lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().sw_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - only for messages
+        return "status"
+
+
+def _check(status: int, what: str):
+    if status != SW_OK:
+        raise SwError(status, what)
+
+
+def _seq(x):
+    """(pointer, length, keepalive) for a numpy array or a torch tensor of residue codes."""
+    if hasattr(x, "data_ptr"):              # torch tensor (host or device)
+        assert x.dtype.itemsize == 1 and x.is_contiguous()
+        return (x.data_ptr() if x.numel() else None), int(x.numel()), x
+    arr = np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+    return (arr.ctypes.data if arr.size else None), int(arr.size), arr
+
+
+def _scoring(matrix, gap_open: int, gap_extend: int):
+    mat = np.ascontiguousarray(np.asarray(matrix, dtype=np.int8))
+    assert mat.ndim == 2 and mat.shape[0] == mat.shape[1]
+    return _Scoring(mat.shape[0], mat.ctypes.data, int(gap_open), int(gap_extend)), mat
+
+
+@dataclass(frozen=True)
+class Hit:
+    score: int
+    a_end: int
+    b_end: int
+
+
+@dataclass(frozen=True)
+class Alignment:
+    score: int
+    a_begin: int
+    a_end: int
+    b_begin: int
+    b_end: int
+    cigar: str
+
+
+class Context:
+    """One sw_ctx: a device and a CUDA stream (a torch stream handle or None)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        handle = None
+        if stream is not None:
+            handle = getattr(stream, "cuda_stream", stream)
+        _check(self._lib.sw_ctx_create(int(device), handle, ctypes.byref(h)), "sw_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self._lib.sw_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def launches(self) -> int:
+        """Kernels launched by this context so far."""
+        return int(self._lib.sw_ctx_launches(self.handle))
+
+    def encode(self, alphabet: str, text) -> np.ndarray:
+        raw = text.encode("ascii") if isinstance(text, str) else bytes(text)
+        buf = np.frombuffer(raw, dtype=np.uint8).copy()
+        out = np.zeros(len(raw), dtype=np.uint8)
+        _check(self._lib.sw_encode(self.handle, alphabet.encode("ascii"),
+                                   buf.ctypes.data if buf.size else None, len(raw),
+                                   out.ctypes.data if out.size else None), "sw_encode")
+        return out
+
+    def score(self, a, b, matrix, gap_open: int, gap_extend: int) -> Hit:
+        pa, m, ka = _seq(a)
+        pb, n, kb = _seq(b)
+        sc, keep = _scoring(matrix, gap_open, gap_extend)
+        hit = _Hit()
+        _check(self._lib.sw_score(self.handle, pa, m, pb, n, ctypes.byref(sc), ctypes.byref(hit)),
+               "sw_score")
+        return Hit(hit.score, hit.a_end, hit.b_end)
+
+    def align(self, a, b, matrix, gap_open: int, gap_extend: int) -> Alignment:
+        pa, m, ka = _seq(a)
+        pb, n, kb = _seq(b)
+        sc, keep = _scoring(matrix, gap_open, gap_extend)
+        aln = _Alignment()
+        _check(self._lib.sw_align(self.handle, pa, m, pb, n, ctypes.byref(sc), ctypes.byref(aln)),
+               "sw_align")
+        try:
+            cig = ctypes.string_at(aln.cigar, aln.cigar_len).decode() if aln.cigar else ""
+        finally:
+            self._lib.sw_alignment_free(ctypes.byref(aln))
+        return Alignment(aln.score, aln.a_begin, aln.a_end, aln.b_begin, aln.b_end, cig)
+
+
+PROBE_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,
+             "viaddmax_s16x2": 4, "vimax3_s16x2_relu": 5, "prmt": 6, "shfl": 7}
+
+
+def probe_int_rates(ctx: Context, iters: int = 2000) -> dict:
+    """Measured thread-level results per SM per clock of each instruction form
+    (sw_probe_int_rate), plus the SM clock seen while they ran."""
+    lib = load()
+    fn = lib.sw_probe_int_rate
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    mhz = []
+    for name, op in PROBE_OPS.items():
+        r, f = ctypes.c_double(), ctypes.c_double()
+        _check(fn(ctx.handle, op, iters, ctypes.byref(r), ctypes.byref(f)), "sw_probe_int_rate")
+        out[name] = round(r.value, 2)
+        mhz.append(f.value)
+    out["sm_mhz"] = round(sum(mhz) / len(mhz), 1)
+    return out

@@ -1,0 +1,385 @@
+// sw_abi.cu -- host runtime behind the C ABI declared in include/sw.h:
+// argument checking, device scratch management, staging of host inputs,
+// launch of the fill / reduction / traceback kernels and assembly of the
+// results.  Every arithmetic step of the alignment runs in the kernels;
+// the host only moves data and formats the CIGAR text.
+#include "sw.h"
+#include "sw_ctx.h"
+#include "wavefront.cuh"
+#include "aux_kernels.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace swgb;
+
+// ------------------------------------------------------------------ helpers
+
+int swgb::DevBuf::ensure(size_t bytes) {
+    if (bytes <= cap) return SW_OK;
+    release();
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return SW_ENOMEM;
+    }
+    cap = bytes;
+    return SW_OK;
+}
+
+void swgb::DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+int swgb::HostBuf::ensure(size_t bytes) {
+    if (bytes <= cap) return SW_OK;
+    release();
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return SW_ENOMEM;
+    }
+    cap = bytes;
+    return SW_OK;
+}
+
+void swgb::HostBuf::release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+}
+
+swgb::DeviceGuard::DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    now = dev;
+}
+
+swgb::DeviceGuard::~DeviceGuard() {
+    if (prev != now) cudaSetDevice(prev);
+}
+
+bool swgb::is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int swgb::check_scoring(const sw_scoring *sc, DevScoring *out) {
+    if (!sc || !sc->matrix) return SW_EINVAL;
+    if (sc->alphabet < 1 || sc->alphabet > kMaxAlphabet) return SW_EINVAL;
+    if (sc->gap_extend < 0 || sc->gap_open < sc->gap_extend || sc->gap_open > 1000000) return SW_EINVAL;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        const int K = sc->alphabet;
+        std::memcpy(out->mat, sc->matrix, (size_t)K * K);
+        out->K = K;
+        out->go = sc->gap_open;
+        out->ge = sc->gap_extend;
+    }
+    return SW_OK;
+}
+
+int swgb::max_pos_score(const sw_scoring *sc) {
+    int mx = 0;
+    for (int k = 0; k < sc->alphabet * sc->alphabet; ++k) mx = std::max(mx, (int)sc->matrix[k]);
+    return mx;
+}
+
+int swgb::stage_seq(sw_ctx *c, const uint8_t *p, int64_t len, DevBuf &buf, const uint8_t **dptr) {
+    if (len == 0) { *dptr = nullptr; return SW_OK; }
+    if (is_device_ptr(p)) { *dptr = p; return SW_OK; }
+    int rc = buf.ensure((size_t)len + 16);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(buf.p, p, (size_t)len, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return SW_ECUDA;
+    *dptr = static_cast<const uint8_t *>(buf.p);
+    return SW_OK;
+}
+
+int swgb::map_kernel_error(int e) {
+    switch (e) {
+        case 0: return SW_OK;
+        case kErrBadCode: return SW_EINVAL;
+        case kErrTimeout: return SW_ETIMEOUT;
+        case kErrOverflow: return SW_ERANGE;
+        default: return SW_ECUDA;
+    }
+}
+
+#define CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; } } while (0)
+#define RC(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+// ------------------------------------------------------------- fill launches
+
+namespace {
+
+template <int R, int W, bool TB>
+int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
+    auto kern = wavefront_kernel<R, W, TB>;
+    constexpr int HC = W * 32 * R;
+    const size_t smem = (size_t)(K + 1) * HC;
+    static int attr_set[64] = {0};
+    if (c->device < 64 && !attr_set[c->device]) {
+        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((kMaxAlphabet + 1) * HC)));
+        attr_set[c->device] = 1;
+    }
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (W + 1) * 32, smem));
+    if (occ < 1) return SW_ECUDA;
+    const long long grid = std::min<long long>(tickets, (long long)occ * c->nsm);
+    kern<<<(unsigned)grid, (W + 1) * 32, smem, c->stream>>>(L);
+    CU(cudaGetLastError());
+    ++c->launches;
+    return SW_OK;
+}
+
+}  // namespace
+
+int swgb::fill_rows_per_strip(const FillConfig &cfg) { return cfg.W * 32 * cfg.R; }
+
+int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const FillLaunch &L, int K,
+                      long long tickets) {
+    if (tickets <= 0) return SW_OK;
+#define CASE(R_, W_)                                                                   \
+    if (cfg.R == R_ && cfg.W == W_)                                                    \
+        return tb ? launch_fill_cfg<R_, W_, true>(c, L, K, tickets)                    \
+                  : launch_fill_cfg<R_, W_, false>(c, L, K, tickets);
+    CASE(4, 2) CASE(4, 4) CASE(8, 2) CASE(8, 4) CASE(8, 8) CASE(16, 4)
+#undef CASE
+    return SW_EINVAL;
+}
+
+// Runs the fill over `tasks` (already in host memory, ticket0 assigned) and
+// leaves the per-strip candidates in c->cand.
+int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const std::vector<FillTask> &tasks,
+                   long long tickets, int K) {
+    const size_t tbytes = tasks.size() * sizeof(FillTask);
+    RC(c->tasks.ensure(tbytes));
+    RC(c->prog.ensure((size_t)tickets * sizeof(int)));
+    RC(c->cand.ensure((size_t)tickets * sizeof(int4)));
+    RC(c->ticket.ensure(sizeof(unsigned long long)));
+    RC(c->stage.ensure(tbytes));
+    std::memcpy(c->stage.p, tasks.data(), tbytes);
+    CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, tbytes, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->prog.p, 0, (size_t)tickets * sizeof(int), c->stream));
+    CU(cudaMemsetAsync(c->ticket.p, 0, sizeof(unsigned long long), c->stream));
+    FillLaunch L;
+    L.tasks = static_cast<const FillTask *>(c->tasks.p);
+    L.scorings = static_cast<const DevScoring *>(c->scorings.p);
+    L.ticket = static_cast<unsigned long long *>(c->ticket.p);
+    L.prog = static_cast<int *>(c->prog.p);
+    L.cand = static_cast<int4 *>(c->cand.p);
+    L.err = static_cast<int *>(c->err.p);
+    L.total = tickets;
+    L.spin_limit = c->spin_limit;
+    L.ntasks = (int)tasks.size();
+    // c->stage is pinned and copied asynchronously: callers synchronise the
+    // stream before they run another fill (every ABI call ends with a sync).
+    return launch_fill(c, cfg, tb, L, K, tickets);
+}
+
+// Upload one or more scoring tables into c->scorings.
+int swgb::upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s) {
+    const size_t bytes = s.size() * sizeof(DevScoring);
+    RC(c->scorings.ensure(bytes));
+    RC(c->stage2.ensure(bytes));
+    std::memcpy(c->stage2.p, s.data(), bytes);
+    CU(cudaMemcpyAsync(c->scorings.p, c->stage2.p, bytes, cudaMemcpyHostToDevice, c->stream));
+    return SW_OK;
+}
+
+int swgb::reset_err(sw_ctx *c) {
+    CU(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream));
+    return SW_OK;
+}
+
+int swgb::validate_codes(sw_ctx *c, const uint8_t *d, int64_t len, int K) {
+    if (len <= 0) return SW_OK;
+    const int threads = 256;
+    const long long blocks = std::min<long long>((len + threads - 1) / threads, 4LL * c->nsm);
+    validate_codes_kernel<<<(unsigned)blocks, threads, 0, c->stream>>>(d, len, K, static_cast<int *>(c->err.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    return SW_OK;
+}
+
+int swgb::read_err(sw_ctx *c, int *e) {
+    RC(c->stage3.ensure(64));
+    CU(cudaMemcpyAsync(c->stage3.p, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    *e = *static_cast<int *>(c->stage3.p);
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------- the ABI
+
+extern "C" {
+
+const char *sw_strerror(int s) {
+    switch (s) {
+        case SW_OK: return "ok";
+        case SW_EINVAL: return "invalid argument";
+        case SW_ENOMEM: return "out of memory";
+        case SW_ECUDA: return "CUDA error";
+        case SW_ETIMEOUT: return "bounded device wait gave up";
+        case SW_EAGAIN: return "resource busy or result not ready";
+        case SW_ERANGE: return "size or score out of range";
+        default: return "unknown status";
+    }
+}
+
+int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
+    if (!out) return SW_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; }
+    if (device < 0 || device >= ndev) return SW_EINVAL;
+    DeviceGuard g(device);
+    sw_ctx *c = new (std::nothrow) sw_ctx();
+    if (!c) return SW_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SW_ECUDA;
+    }
+    int rc = c->err.ensure(256);
+    if (!rc) rc = c->stage3.ensure(256);
+    if (rc) { delete c; return rc; }
+    if (cudaMemsetAsync(c->err.p, 0, 256, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SW_ECUDA;
+    }
+    const char *ev = std::getenv("SWGB_SPIN_LIMIT");
+    c->spin_limit = ev ? std::atoll(ev) : (1LL << 26);
+    c->fwd = FillConfig{8, 4};
+    c->tbc = FillConfig{8, 4};
+    c->ckpt_budget = (size_t)4 << 30;
+    c->tb_budget = (size_t)4 << 30;
+    *out = c;
+    return SW_OK;
+}
+
+void sw_ctx_destroy(sw_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+int sw_encode(sw_ctx *c, const char *alphabet, const char *text, int64_t len, uint8_t *codes) {
+    if (!c || !alphabet || len < 0 || (len > 0 && (!text || !codes))) return SW_EINVAL;
+    const size_t K = std::strlen(alphabet);
+    if (K < 1 || K > (size_t)kMaxAlphabet) return SW_EINVAL;
+    uint8_t table[256];
+    std::memset(table, 255, sizeof(table));
+    for (size_t k = 0; k < K; ++k) {
+        const unsigned char ch = (unsigned char)alphabet[k];
+        if (table[ch] != 255) return SW_EINVAL;     // repeated letter
+        table[ch] = (uint8_t)k;
+        if (ch >= 'A' && ch <= 'Z') table[ch - 'A' + 'a'] = (uint8_t)k;
+    }
+    if (len == 0) return SW_OK;
+    DeviceGuard g(c->device);
+    const uint8_t *dtext = nullptr;
+    RC(stage_seq(c, reinterpret_cast<const uint8_t *>(text), len, c->seq_a, &dtext));
+    const bool dev_out = is_device_ptr(codes);
+    uint8_t *dcodes = codes;
+    if (!dev_out) {
+        RC(c->seq_b.ensure((size_t)len + 16));
+        dcodes = static_cast<uint8_t *>(c->seq_b.p);
+    }
+    RC(c->misc.ensure(256 + 16));
+    RC(c->stage2.ensure(256 + 16));
+    std::memcpy(c->stage2.p, table, 256);
+    const unsigned long long none = ~0ULL;
+    std::memcpy(static_cast<char *>(c->stage2.p) + 256, &none, 8);
+    CU(cudaMemcpyAsync(c->misc.p, c->stage2.p, 264, cudaMemcpyHostToDevice, c->stream));
+    uint8_t *dtable = static_cast<uint8_t *>(c->misc.p);
+    unsigned long long *dbad = reinterpret_cast<unsigned long long *>(dtable + 256);
+    const long long blocks = std::min<long long>((len + 255) / 256, 8LL * c->nsm);
+    encode_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(dtext, len, dtable, dcodes, dbad);
+    CU(cudaGetLastError());
+    ++c->launches;
+    CU(cudaMemcpyAsync(c->stage3.p, dbad, 8, cudaMemcpyDeviceToHost, c->stream));
+    if (!dev_out) CU(cudaMemcpyAsync(codes, dcodes, (size_t)len, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    unsigned long long bad;
+    std::memcpy(&bad, c->stage3.p, 8);
+    return bad == ~0ULL ? SW_OK : SW_EINVAL;
+}
+
+int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+             const sw_scoring *sc, sw_hit *out) {
+    if (!c || !out) return SW_EINVAL;
+    DevScoring ds;
+    RC(check_scoring(sc, &ds));
+    if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
+    if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
+    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    if (m == 0 || n == 0) { *out = sw_hit{0, 0, 0, 0}; return SW_OK; }
+    DeviceGuard g(c->device);
+    const uint8_t *da, *db;
+    RC(stage_seq(c, a, m, c->seq_a, &da));
+    RC(stage_seq(c, b, n, c->seq_b, &db));
+    RC(reset_err(c));
+    RC(validate_codes(c, da, m, ds.K));
+    RC(validate_codes(c, db, n, ds.K));
+    RC(upload_scorings(c, {ds}));
+
+    const int HC = fill_rows_per_strip(c->fwd);
+    FillTask t{};
+    t.a = da; t.b = db;
+    t.rows = (int32_t)m; t.ncols = (int32_t)n;
+    t.nstrips = (int32_t)((m + HC - 1) / HC);
+    t.scoring = 0; t.ticket0 = 0;
+    t.top = nullptr;
+    t.nslot = std::min(t.nstrips, 4);
+    RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
+    t.bnd = static_cast<int2 *>(c->bnd.p);
+    t.ckpt_every = 0; t.ckpt = nullptr; t.row0 = 0; t.tb = nullptr; t.tb_ld = 0;
+    RC(run_fill(c, c->fwd, false, {t}, t.nstrips, ds.K));
+
+    RC(c->result.ensure(sizeof(int4)));
+    reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,
+                                                       static_cast<const int4 *>(c->cand.p),
+                                                       static_cast<int4 *>(c->result.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    CU(cudaMemcpyAsync(c->stage3.p, c->result.p, sizeof(int4), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 16, c->err.p, sizeof(int),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    int4 res;
+    int e;
+    std::memcpy(&res, c->stage3.p, sizeof(int4));
+    std::memcpy(&e, static_cast<char *>(c->stage3.p) + 16, sizeof(int));
+    RC(map_kernel_error(e));
+    *out = sw_hit{res.x, 0, (int64_t)res.y, (int64_t)res.z};
+    return SW_OK;
+}
+
+int64_t sw_ctx_launches(const sw_ctx *c) { return c ? c->launches : -1; }
+
+void sw_alignment_free(sw_alignment *aln) {
+    if (!aln) return;
+    std::free(aln->cigar);
+    aln->cigar = nullptr;
+    aln->cigar_len = 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// sw_ctx.h -- internal host-side declarations of libswgb: the context,
+// device/pinned buffers and the helpers the ABI translation units share.
+#pragma once
+#include "sw.h"
+#include "sw_device.cuh"
+#include "wavefront.cuh"
+
+#include <cstddef>
+#include <vector>
+
+namespace swgb {
+
+// Grow-only device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes);
+    void release();
+    ~DevBuf() { release(); }
+};
+
+// Grow-only pinned host allocation (staging for asynchronous copies).
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes);
+    void release();
+    ~HostBuf() { release(); }
+};
+
+struct DeviceGuard {
+    int prev = 0, now = 0;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+// Tile shape of the wavefront fill: R rows per lane, W compute warps.
+struct FillConfig {
+    int R;
+    int W;
+};
+
+}  // namespace swgb
+
+struct sw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 0;
+    long long spin_limit = 0;
+    long long launches = 0;           // kernels launched by this context
+    swgb::FillConfig fwd{8, 4};       // score / forward pass
+    swgb::FillConfig tbc{8, 4};       // traceback recompute
+    size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
+    size_t tb_budget = 0;             // bytes of traceback bits per row group
+    swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, tb,
+        tbbnd, runs, walk, misc;
+    swgb::HostBuf stage, stage2, stage3;
+};
+
+namespace swgb {
+
+bool is_device_ptr(const void *p);
+int check_scoring(const sw_scoring *sc, DevScoring *out);
+int max_pos_score(const sw_scoring *sc);
+int stage_seq(sw_ctx *c, const uint8_t *p, int64_t len, DevBuf &buf, const uint8_t **dptr);
+int map_kernel_error(int e);
+int fill_rows_per_strip(const FillConfig &cfg);
+int launch_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const FillLaunch &L, int K, long long tickets);
+int run_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const std::vector<FillTask> &tasks,
+             long long tickets, int K);
+int upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s);
+int reset_err(sw_ctx *c);
+int validate_codes(sw_ctx *c, const uint8_t *d, int64_t len, int K);
+int read_err(sw_ctx *c, int *e);
+
+}  // namespace swgb

@@ -1,0 +1,60 @@
+// sw_device.cuh -- device-side building blocks shared by the kernels of
+// libswgb: constants, the scoring table, packed-byte helpers and the
+// inter-block progress flags.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swgb {
+
+constexpr int kNeg = -(1 << 30);      // stands for -infinity in int32 lanes
+constexpr int kPadScore = -128;       // profile value of padding rows / columns
+constexpr int kMaxAlphabet = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Error codes written by kernels into the context's error word.
+constexpr int kErrTimeout = 1;        // a bounded inter-block wait gave up
+constexpr int kErrBadCode = 2;        // a residue code >= alphabet
+constexpr int kErrOverflow = 3;       // a score would leave the int32 range
+
+struct DevScoring {
+    int8_t mat[kMaxAlphabet * kMaxAlphabet];   // mat[x*K + y]: a-residue x vs b-residue y
+    int32_t K;
+    int32_t go;     // gap open (positive, subtracted)
+    int32_t ge;     // gap extend (positive, subtracted)
+    int32_t pad_;
+};
+
+// Sign-extend byte k of w to int32 with one byte permute (prmt with the
+// sign-replicate selector bit).
+template <int k>
+__device__ __forceinline__ int sext8(uint32_t w) {
+    constexpr uint32_t sel = k | ((8 | k) << 4) | ((8 | k) << 8) | ((8 | k) << 12);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(w), "n"(sel));
+    return static_cast<int>(d);
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) {
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+// Lexicographic order of end-cell candidates: larger score, then smaller
+// column j, then smaller row i.
+__device__ __forceinline__ bool cand_better(int s1, int j1, int i1, int s2, int j2, int i2) {
+    if (s1 != s2) return s1 > s2;
+    if (j1 != j2) return j1 < j2;
+    return i1 < i2;
+}
+
+}  // namespace swgb

@@ -1,0 +1,174 @@
+"""GPU parity of the pairwise path (sw_score, sw_align) against the CPU oracle.
+
+Every case compares score, end cell, begin cell and CIGAR exactly (integer
+work: bit-exact).  Inputs come from the seeded generators shared with the
+oracle tests.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from bruteforce import rescore
+from paper_2211_10769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2211_10769_gb300 import binding, build
+    build.build()
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def _score_case(ctx, oracle_mod, a, b, S, o, e):
+    want = oracle_mod.sw_score(a, b, S, o, e)
+    got = ctx.score(a, b, S, o, e)
+    assert (got.score, got.a_end, got.b_end) == want, (len(a), len(b), o, e)
+
+
+def _align_case(ctx, oracle_mod, a, b, S, o, e):
+    want = oracle_mod.sw_align(a, b, S, o, e)
+    got = ctx.align(a, b, S, o, e)
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end, got.cigar) == \
+        (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end, want.cigar), (len(a), len(b))
+
+
+EDGE_LENGTHS = [0, 1, 2, 31, 32, 33, 63, 64, 65, 255, 256, 257, 1023, 1024, 1025, 2049]
+
+
+@pytest.mark.parametrize("m", [1, 33, 1024, 1025, 3000])
+def test_score_edge_lengths_dna(ctx, oracle_mod, m):
+    sc = W.dna_scoring()
+    for n in EDGE_LENGTHS:
+        a = W.uniform_dna(m, W.BASE_SEED + 5000 + m)
+        b = W.mutate(a, 4, W.BASE_SEED + 6000 + n)[:n] if n else np.zeros(0, np.uint8)
+        if len(b) < n:
+            b = np.concatenate([b, W.uniform_dna(n - len(b), W.BASE_SEED + 7000 + n)])
+        _score_case(ctx, oracle_mod, a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+
+
+def test_score_random_scorings(ctx, oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 8000)
+    for t in range(60):
+        K = int(g.integers(1, 25))
+        m, n = int(g.integers(0, 1500)), int(g.integers(0, 1500))
+        a = g.integers(0, K, size=m).astype(np.uint8)
+        b = g.integers(0, K, size=n).astype(np.uint8)
+        S = g.integers(-6, 8, size=(K, K)).astype(np.int8)
+        o = int(g.integers(0, 12))
+        e = int(g.integers(0, o + 1))
+        _score_case(ctx, oracle_mod, a, b, S, o, e)
+
+
+def test_score_protein_homologs(ctx, oracle_mod):
+    sc = W.protein_scoring()
+    for t in range(8):
+        a = W.random_protein(300 + 211 * t, W.BASE_SEED + 8100 + t)
+        b = W.mutate(a, 20, W.BASE_SEED + 8200 + t, p_sub=0.3)
+        _score_case(ctx, oracle_mod, a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+        _score_case(ctx, oracle_mod, b, a, sc.matrix, sc.gap_open, sc.gap_extend)
+
+
+def test_score_ties_and_degenerate(ctx, oracle_mod):
+    sc = W.dna_scoring()
+    runs = np.zeros(700, np.uint8)                      # one long run of one base
+    _score_case(ctx, oracle_mod, runs, runs, sc.matrix, sc.gap_open, sc.gap_extend)
+    alt = (np.arange(900) % 2).astype(np.uint8)         # many equal maxima
+    _score_case(ctx, oracle_mod, alt, alt[::-1].copy(), sc.matrix, sc.gap_open, sc.gap_extend)
+    mism = np.zeros(500, np.uint8)
+    _score_case(ctx, oracle_mod, mism, mism + 1, sc.matrix, sc.gap_open, sc.gap_extend)   # score 0
+    zero_gap = np.ones((4, 4), np.int8)
+    _score_case(ctx, oracle_mod, runs[:300], alt[:400], zero_gap, 0, 0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_align_random(ctx, oracle_mod, seed):
+    g = np.random.default_rng(W.BASE_SEED + 9000 + seed)
+    dna, prot = W.dna_scoring(), W.protein_scoring()
+    for t in range(6):
+        if t % 2 == 0:
+            A = W.uniform_dna(int(g.integers(1, 3000)), W.BASE_SEED + 9100 + 10 * seed + t)
+            B = W.mutate(A, 4, W.BASE_SEED + 9200 + 10 * seed + t, p_sub=0.1, p_indel=0.02)
+            sc = dna
+        else:
+            A = W.random_protein(int(g.integers(1, 2000)), W.BASE_SEED + 9100 + 10 * seed + t)
+            B = W.mutate(A, 20, W.BASE_SEED + 9200 + 10 * seed + t, p_sub=0.3, p_indel=0.03)
+            sc = prot
+        _align_case(ctx, oracle_mod, A, B, sc.matrix, sc.gap_open, sc.gap_extend)
+
+
+def test_align_gappy_small(ctx, oracle_mod):
+    g = np.random.default_rng(W.BASE_SEED + 9300)
+    S = np.full((4, 4), -3, np.int8)
+    np.fill_diagonal(S, 6)
+    for t in range(40):
+        m, n = int(g.integers(0, 200)), int(g.integers(0, 200))
+        a = g.integers(0, 4, size=m).astype(np.uint8)
+        b = g.integers(0, 4, size=n).astype(np.uint8)
+        o = int(g.integers(1, 5))
+        e = int(g.integers(0, o + 1))
+        _align_case(ctx, oracle_mod, a, b, S, o, e)
+
+
+def test_dna_2k_golden(ctx):
+    rec = json.load(open(os.path.join(GOLDEN, "dna_2k.json")))
+    a, b = W.dna_pair_2k()
+    sc = W.dna_scoring()
+    got = ctx.align(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+        (rec["score"], rec["a_begin"], rec["a_end"], rec["b_begin"], rec["b_end"])
+    import hashlib
+    assert hashlib.sha256(got.cigar.encode()).hexdigest() == rec["cigar_sha256"]
+
+
+def test_long_pair_golden(ctx):
+    path = os.path.join(GOLDEN, "dna_200k.json")
+    rec = json.load(open(path))
+    a, b = W.dna_long_pair(200_000)
+    sc = W.dna_scoring()
+    hit = ctx.score(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    assert (hit.score, hit.a_end, hit.b_end) == (rec["score"], rec["a_end"], rec["b_end"])
+    got = ctx.align(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+        (rec["score"], rec["a_begin"], rec["a_end"], rec["b_begin"], rec["b_end"])
+    import hashlib
+    assert len(got.cigar) == rec["cigar_len"]
+    assert got.cigar[:120] == rec["cigar_head"] and got.cigar[-120:] == rec["cigar_tail"]
+    assert hashlib.sha256(got.cigar.encode()).hexdigest() == rec["cigar_sha256"]
+    assert rescore(a, b, sc.matrix, sc.gap_open, sc.gap_extend, got.a_begin, got.b_begin,
+                   got.cigar) == (got.score, got.a_end, got.b_end)
+
+
+def test_device_pointers_and_encode(ctx, oracle_mod):
+    import torch
+    sc = W.dna_scoring()
+    a, b = W.dna_pair_2k()
+    ta = torch.from_numpy(a).cuda()
+    tb = torch.from_numpy(b).cuda()
+    assert ctx.score(ta, tb, sc.matrix, sc.gap_open, sc.gap_extend) == ctx.score(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    txt = "".join("ACGT"[x] for x in a[:500])
+    assert (ctx.encode("ACGT", txt) == a[:500]).all()
+    assert (ctx.encode("ACGT", txt.lower()) == oracle_mod.encode("ACGT", txt)).all()
+
+
+def test_invalid_arguments(ctx):
+    from paper_2211_10769_gb300 import binding
+    sc = W.dna_scoring()
+    a = W.uniform_dna(100, 1)
+    bad = a.copy()
+    bad[50] = 4
+    with pytest.raises(binding.SwError) as ei:
+        ctx.score(a, bad, sc.matrix, sc.gap_open, sc.gap_extend)
+    assert ei.value.status == binding.SW_EINVAL
+    with pytest.raises(binding.SwError):
+        ctx.score(a, a, sc.matrix, 1, 2)                    # extend > open
+    with pytest.raises(binding.SwError):
+        ctx.encode("ACGT", "ACGN")
+    # the context stays usable after errors
+    assert ctx.score(a, a, sc.matrix, sc.gap_open, sc.gap_extend).score == 100
