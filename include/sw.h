@@ -157,6 +157,29 @@ int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t
 void sw_alignment_free(sw_alignment *aln);
 
 /*
+ * sw_score without any device allocation (the paper has no counterpart; it
+ * exists for callers of this library that cannot call cudaMalloc, such as a
+ * serving process whose own caching allocator owns the device memory
+ * budget, or a latency-critical pipeline that must avoid the implicit
+ * device synchronisation of cudaMalloc / cudaFree).
+ *
+ * Same result as sw_score (score and canonical end cell).  No context is
+ * needed: it runs on the current CUDA device, on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream).  a and b must be device
+ * memory (else SW_EINVAL); out is host memory.  All scratch lives in one
+ * fixed array of about 4.3 MB inside the library, which every GPU that
+ * loads the library holds until the process exits.  Limits: n <= 262,144
+ * columns and m <= 16,384 * 1,024 = 16,777,216 rows; larger inputs are
+ * rejected with SW_ERANGE.  The first call on each device looks up the
+ * array's device address and must be made with that device current, before
+ * any stream capture.  Calls share the array: calls whose GPU work could
+ * overlap (other streams, other host threads) race and must be serialised
+ * by the caller.  Synchronous: returns after the result is on the host.
+ */
+int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                     const sw_scoring *sc, sw_hit *out);
+
+/*
  * Number of kernels this context has launched since it was created
  * (diagnostics: lets a caller count device launches per call).  Returns -1
  * for a null context.
