@@ -125,9 +125,9 @@ int swgb::map_kernel_error(int e) {
 
 namespace {
 
-template <int R, int W, bool TB>
+template <int R, int W, int MODE, bool FOLD>
 int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
-    auto kern = wavefront_kernel<R, W, TB>;
+    auto kern = wavefront_kernel<R, W, MODE, FOLD>;
     constexpr int HC = W * 32 * R;
     const size_t smem = (size_t)(K + 1) * HC;
     static int attr_set[64] = {0};
@@ -146,26 +146,43 @@ int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
     return SW_OK;
 }
 
+template <int R, int W>
+int launch_fill_rw(sw_ctx *c, int mode, bool fold, const FillLaunch &L, int K, long long tickets) {
+    switch (mode * 2 + (fold ? 1 : 0)) {
+        case 0: return launch_fill_cfg<R, W, kModeScore, false>(c, L, K, tickets);
+        case 1: return launch_fill_cfg<R, W, kModeScore, true>(c, L, K, tickets);
+        case 2: return launch_fill_cfg<R, W, kModeScoreCk, false>(c, L, K, tickets);
+        case 3: return launch_fill_cfg<R, W, kModeScoreCk, true>(c, L, K, tickets);
+        case 4: return launch_fill_cfg<R, W, kModeTb, false>(c, L, K, tickets);
+        case 5: return launch_fill_cfg<R, W, kModeTb, true>(c, L, K, tickets);
+        default: return SW_EINVAL;
+    }
+}
+
 }  // namespace
 
 int swgb::fill_rows_per_strip(const FillConfig &cfg) { return cfg.W * 32 * cfg.R; }
 
-int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const FillLaunch &L, int K,
+bool swgb::fold_open(const DevScoring &s) {
+    int lo = 127, hi = -128;
+    for (int k = 0; k < s.K * s.K; ++k) { lo = std::min(lo, (int)s.mat[k]); hi = std::max(hi, (int)s.mat[k]); }
+    return hi + s.go <= 127 && lo + s.go >= -128;
+}
+
+int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                       long long tickets) {
     if (tickets <= 0) return SW_OK;
-#define CASE(R_, W_)                                                                   \
-    if (cfg.R == R_ && cfg.W == W_)                                                    \
-        return tb ? launch_fill_cfg<R_, W_, true>(c, L, K, tickets)                    \
-                  : launch_fill_cfg<R_, W_, false>(c, L, K, tickets);
-    CASE(4, 2) CASE(4, 4) CASE(8, 2) CASE(8, 4) CASE(8, 8) CASE(16, 4)
-#undef CASE
+    if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets);
+    if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets);
+    if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets);
+    if (cfg.R == 16 && cfg.W == 4) return launch_fill_rw<16, 4>(c, mode, fold, L, K, tickets);
     return SW_EINVAL;
 }
 
 // Runs the fill over `tasks` (already in host memory, ticket0 assigned) and
 // leaves the per-strip candidates in c->cand.
-int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const std::vector<FillTask> &tasks,
-                   long long tickets, int K) {
+int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
+                   const std::vector<FillTask> &tasks, long long tickets, int K) {
     const size_t tbytes = tasks.size() * sizeof(FillTask);
     RC(c->tasks.ensure(tbytes));
     RC(c->prog.ensure((size_t)tickets * sizeof(int)));
@@ -188,7 +205,7 @@ int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const std::vector<
     L.ntasks = (int)tasks.size();
     // c->stage is pinned and copied asynchronously: callers synchronise the
     // stream before they run another fill (every ABI call ends with a sync).
-    return launch_fill(c, cfg, tb, L, K, tickets);
+    return launch_fill(c, cfg, mode, fold, L, K, tickets);
 }
 
 // Upload one or more scoring tables into c->scorings.
@@ -268,6 +285,9 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     c->spin_limit = ev ? std::atoll(ev) : (1LL << 26);
     c->fwd = FillConfig{8, 4};
     c->tbc = FillConfig{8, 4};
+    // tuning overrides: SWGB_FWD="R,W" and SWGB_TB="R,W" (tile shapes of the fills)
+    if (const char *f = std::getenv("SWGB_FWD")) std::sscanf(f, "%d,%d", &c->fwd.R, &c->fwd.W);
+    if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     c->ckpt_budget = (size_t)4 << 30;
     c->tb_budget = (size_t)4 << 30;
     *out = c;
@@ -352,7 +372,7 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
     t.bnd = static_cast<int2 *>(c->bnd.p);
     t.ckpt_every = 0; t.ckpt = nullptr; t.row0 = 0; t.tb = nullptr; t.tb_ld = 0;
-    RC(run_fill(c, c->fwd, false, {t}, t.nstrips, ds.K));
+    RC(run_fill(c, c->fwd, kModeScore, fold_open(ds), {t}, t.nstrips, ds.K));
 
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,

@@ -2,22 +2,24 @@
 // the best score, reconstruction recovers the path with space-efficient
 // methods).
 //
-// 1. Forward fill over the whole matrix (score mode), keeping the bottom
-//    row (H, F per column) of strips as checkpoint rows: every strip while
-//    that fits the checkpoint budget, else every k-th strip.
+// 1. Forward fill over the whole matrix (score mode with checkpoints): the
+//    H / F row at every BT-th row and the H / E column at every BT-th
+//    column are kept.  BT is a power of two chosen so that both sets of
+//    checkpoints fit the checkpoint budget, so memory is O((m + n)^2 / BT)
+//    rather than m x n.
 // 2. The end cell (ie, je) comes from the per-strip candidates.
-// 3. Blocks are the row ranges between consecutive checkpoint rows, cut at
-//    row ie and column je.  Going upwards from the block holding ie, groups
-//    of blocks whose decision bits fit the traceback budget are recomputed
-//    from their checkpoint rows (traceback mode; the blocks of a group are
-//    independent tasks of one launch) and the walk kernel follows the bits
-//    through the group, carrying its cell and state to the next group.
-// Memory is (rows / checkpoint spacing) x n checkpoint entries plus one
-// group of bits, instead of the m x n matrix; the recomputation touches at
-// most ie x je cells.
+// 3. With checkpoints on both sides, every BT x BT tile can be recomputed
+//    on its own from its top row, left column and corner.  The walk goes
+//    in rounds: recompute the decision bits of a diagonal band of tiles
+//    from the walk's current tile towards the upper left (traceback mode,
+//    every tile an independent task of one launch), walk the path through
+//    them, and start the next band where the walk left the computed tiles.
+//    Only tiles near the path are recomputed.
+// 4. The run records of the walk become the CIGAR text on the host.
 #include "sw.h"
 #include "sw_ctx.h"
 #include "wavefront.cuh"
+#include "walk.cuh"
 #include "aux_kernels.cuh"
 
 #include <algorithm>
@@ -33,21 +35,8 @@ using namespace swgb;
 
 namespace {
 
-int launch_walk(sw_ctx *c, int R, const void *tb, long long ld, int G0) {
-    WalkState *st = static_cast<WalkState *>(c->walk.p);
-    int2 *runs = static_cast<int2 *>(c->runs.p);
-    switch (R) {
-        case 4: walk_kernel<uint16_t, 4><<<1, 32, 0, c->stream>>>(static_cast<const uint16_t *>(tb), ld, G0, st, runs); break;
-        case 8: walk_kernel<uint32_t, 8><<<1, 32, 0, c->stream>>>(static_cast<const uint32_t *>(tb), ld, G0, st, runs); break;
-        case 16: walk_kernel<unsigned long long, 16><<<1, 32, 0, c->stream>>>(static_cast<const unsigned long long *>(tb), ld, G0, st, runs); break;
-        default: return SW_EINVAL;
-    }
-    CU(cudaGetLastError());
-    ++c->launches;
-    return SW_OK;
-}
-
-int tb_word_bytes(int R) { return R / 2; }
+constexpr int kBandDepth = 16;            // tile rows per band (three tiles per tile row)
+constexpr long long kWalkMaxIters = 1LL << 26;
 
 int empty_alignment(sw_alignment *out) {
     char *s = static_cast<char *>(std::malloc(1));
@@ -55,6 +44,27 @@ int empty_alignment(sw_alignment *out) {
     s[0] = 0;
     *out = sw_alignment{0, 0, 0, 0, 0, 0, s, 0};
     return SW_OK;
+}
+
+template <typename Word>
+int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT, int R) {
+    TileTable<Word> T;
+    T.bits = reinterpret_cast<const Word *const *>(table);
+    T.I0 = I0; T.J0 = J0; T.nI = nI; T.nJ = nJ; T.BT = BT; T.R = R;
+    walk_kernel<Word><<<1, 32, 0, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
+                                                static_cast<int2 *>(c->runs.p), kWalkMaxIters);
+    CU(cudaGetLastError());
+    ++c->launches;
+    return SW_OK;
+}
+
+int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT, int R) {
+    switch (R) {
+        case 4: return launch_walk_t<uint16_t>(c, table, I0, J0, nI, nJ, BT, R);
+        case 8: return launch_walk_t<uint32_t>(c, table, I0, J0, nI, nJ, BT, R);
+        case 16: return launch_walk_t<unsigned long long>(c, table, I0, J0, nI, nJ, BT, R);
+        default: return SW_EINVAL;
+    }
 }
 
 }  // namespace
@@ -76,33 +86,37 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(validate_codes(c, da, m, ds.K));
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
+    const bool fold = fold_open(ds);
 
-    // ---- 1. forward fill with checkpoint rows
+    // ---- tile side: both checkpoint sets within the budget
     const int HC = fill_rows_per_strip(c->fwd);
     const int HT = fill_rows_per_strip(c->tbc);
-    if (HC % HT != 0) return SW_EINVAL;
+    long long BT = std::max(HC, HT);
+    BT = std::max(BT, 1024LL);
+    auto ck_bytes = [&](long long bt) {
+        return (size_t)((m / bt) * n + (n / bt) * m) * sizeof(int2);
+    };
+    while (ck_bytes(BT) > c->ckpt_budget && BT < (1LL << 30)) BT *= 2;
+    if (BT % HC != 0 || BT % HT != 0) return SW_EINVAL;
+    const long long nrowck = std::max<long long>(1, m / BT), ncolck = std::max<long long>(1, n / BT);
+
+    // ---- 1. forward fill with row and column checkpoints
     FillTask t{};
     t.a = da; t.b = db;
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
     t.nstrips = (int32_t)((m + HC - 1) / HC);
-    t.scoring = 0; t.ticket0 = 0; t.top = nullptr; t.row0 = 0;
-    const size_t row_bytes = (size_t)n * sizeof(int2);
-    int every = 1;                                    // strips per checkpoint
-    while ((size_t)(t.nstrips / every) * row_bytes > c->ckpt_budget && every < t.nstrips) every *= 2;
-    if (every == 1) {
-        t.nslot = t.nstrips;                          // every strip's bottom row stays
-        RC(c->bnd.ensure((size_t)t.nslot * row_bytes));
-        t.bnd = static_cast<int2 *>(c->bnd.p);
-        t.ckpt_every = 0; t.ckpt = nullptr;
-    } else {
-        t.nslot = std::min(t.nstrips, 4);
-        RC(c->bnd.ensure((size_t)t.nslot * row_bytes));
-        t.bnd = static_cast<int2 *>(c->bnd.p);
-        t.ckpt_every = every;
-        RC(c->ckpt.ensure((size_t)std::max(1, t.nstrips / every) * row_bytes));
-        t.ckpt = static_cast<int2 *>(c->ckpt.p);
-    }
-    RC(run_fill(c, c->fwd, false, {t}, t.nstrips, ds.K));
+    t.scoring = 0; t.ticket0 = 0; t.top = nullptr; t.left = nullptr; t.corner = nullptr; t.row0 = 0;
+    t.nslot = std::min(t.nstrips, 4);
+    RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
+    t.bnd = static_cast<int2 *>(c->bnd.p);
+    t.ckpt_every = (int32_t)(BT / HC);
+    RC(c->ckpt.ensure((size_t)nrowck * (size_t)n * sizeof(int2)));
+    t.ckpt = static_cast<int2 *>(c->ckpt.p);
+    t.colck_every = (int32_t)BT;
+    t.colck_ld = m;
+    RC(c->colck.ensure((size_t)ncolck * (size_t)m * sizeof(int2)));
+    t.colck = static_cast<int2 *>(c->colck.p);
+    RC(run_fill(c, c->fwd, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,
                                                        static_cast<const int4 *>(c->cand.p),
@@ -124,64 +138,64 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     // ---- 2. walk state
     RC(c->walk.ensure(sizeof(WalkState)));
     RC(c->runs.ensure((size_t)(ie + je + 2) * sizeof(int2)));
-    WalkState w0{ie, je, 0, 0, 0, -1, 0};
-    std::memcpy(c->stage2.p, &w0, sizeof(w0));
-    CU(cudaMemcpyAsync(c->walk.p, c->stage2.p, sizeof(w0), cudaMemcpyHostToDevice, c->stream));
+    WalkState w{ie, je, 0, 0, 0, -1, 0};
+    const size_t table_cap = (size_t)(kBandDepth + 1) * (kBandDepth + 2);
+    RC(c->stage2.ensure(std::max(sizeof(WalkState), table_cap * sizeof(void *))));
+    std::memcpy(c->stage2.p, &w, sizeof(w));
+    CU(cudaMemcpyAsync(c->walk.p, c->stage2.p, sizeof(w), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
 
-    // ---- 3. groups of checkpoint blocks, bottom-up
-    const long long BR = (long long)HC * every;       // rows per block
-    const int nblocks = (int)((ie + BR - 1) / BR);
-    auto block_rows = [&](int bk) { return (int)std::min<long long>(BR, ie - bk * BR); };
-    auto ckpt_row = [&](int bk) -> const int2 * {     // bottom row of block bk-1
-        if (bk == 0) return nullptr;
-        if (every == 1) return t.bnd + (size_t)(bk - 1) * n;
-        return t.ckpt + (size_t)(bk - 1) * n;
-    };
-    const int wb = tb_word_bytes(c->tbc.R);
-    WalkState w = w0;
-    int hi = nblocks - 1;
-    while (hi >= 0 && !w.done) {
-        // largest group [lo, hi] whose bits fit the budget (at least one block)
-        int lo = hi;
-        auto group_bytes = [&](int l) {
-            long long rows = (long long)(hi - l) * BR + ((block_rows(hi) + HT - 1) / HT) * (long long)HT;
-            return (size_t)(rows / c->tbc.R) * (size_t)je * wb;
-        };
-        while (lo > 0 && group_bytes(lo - 1) <= c->tb_budget) --lo;
-        RC(c->tb.ensure(group_bytes(lo)));
+    // ---- 3. rounds: recompute a band of tiles, walk through it
+    const int R = c->tbc.R;
+    const size_t tile_words = (size_t)(BT / R) * (size_t)BT;
+    const size_t tile_bytes = tile_words * (size_t)(R / 2);
+    const int maxtiles = 3 * kBandDepth;
+    RC(c->tb.ensure(tile_bytes * maxtiles));
+    RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
+    RC(c->misc.ensure(table_cap * sizeof(void *)));
+    const int2 *rowck = t.ckpt, *colck = t.colck;
+    int prev_i = -1, prev_j = -1, prev_state = -1;
+    while (true) {
+        const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
+        const int I0 = std::max(0, I - kBandDepth + 1), J0 = std::max(0, J - kBandDepth);
+        const int nI = I - I0 + 1, nJ = J - J0 + 1;
+        std::vector<const void *> table((size_t)nI * nJ, nullptr);
         std::vector<FillTask> tasks;
         long long tickets = 0;
-        size_t bnd_need = 0;
-        for (int bk = lo; bk <= hi; ++bk) {
-            const int rows = block_rows(bk);
-            const int ns = (rows + HT - 1) / HT;
-            bnd_need += (size_t)std::min(ns, 2) * (size_t)je * sizeof(int2);
+        for (int d = 0; d < kBandDepth && I - d >= 0; ++d) {
+            for (int dl = -1; dl <= 1; ++dl) {
+                const int ti = I - d, tj = J - d + dl;
+                if (tj < 0 || tj > J) continue;
+                FillTask u{};
+                const long long r0 = (long long)ti * BT, c0 = (long long)tj * BT;
+                u.a = da + r0;
+                u.b = db + c0;
+                u.rows = (int32_t)std::min<long long>(BT, m - r0);
+                u.ncols = (int32_t)std::min<long long>(BT, n - c0);
+                u.nstrips = (u.rows + HT - 1) / HT;
+                u.scoring = 0;
+                u.ticket0 = tickets;
+                u.top = ti > 0 ? rowck + (size_t)(ti - 1) * n + c0 : nullptr;
+                u.left = tj > 0 ? colck + (size_t)(tj - 1) * m + r0 : nullptr;
+                u.corner = (ti > 0 && tj > 0) ? colck + (size_t)(tj - 1) * m + r0 - 1 : nullptr;
+                const size_t k = tasks.size();
+                u.nslot = std::min(u.nstrips, 2);
+                u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;
+                u.ckpt_every = 0; u.ckpt = nullptr; u.colck = nullptr; u.colck_every = 0;
+                u.row0 = (int32_t)r0;
+                u.tb = static_cast<char *>(c->tb.p) + k * tile_bytes;
+                u.tb_ld = BT;
+                tickets += u.nstrips;
+                tasks.push_back(u);
+                table[(size_t)(ti - I0) * nJ + (tj - J0)] = u.tb;
+            }
         }
-        RC(c->tbbnd.ensure(bnd_need));
-        size_t bnd_off = 0;
-        for (int bk = lo; bk <= hi; ++bk) {
-            FillTask u{};
-            const int rows = block_rows(bk);
-            u.a = da + (size_t)bk * BR;
-            u.b = db;
-            u.rows = rows;
-            u.ncols = je;
-            u.nstrips = (rows + HT - 1) / HT;
-            u.scoring = 0;
-            u.ticket0 = tickets;
-            u.top = ckpt_row(bk);
-            u.nslot = std::min(u.nstrips, 2);
-            u.bnd = reinterpret_cast<int2 *>(static_cast<char *>(c->tbbnd.p) + bnd_off);
-            bnd_off += (size_t)u.nslot * (size_t)je * sizeof(int2);
-            u.ckpt_every = 0; u.ckpt = nullptr;
-            u.row0 = (int32_t)(bk * BR);
-            u.tb = static_cast<char *>(c->tb.p) + (size_t)((bk - lo) * BR / c->tbc.R) * (size_t)je * wb;
-            u.tb_ld = je;
-            tickets += u.nstrips;
-            tasks.push_back(u);
-        }
-        RC(run_fill(c, c->tbc, true, tasks, tickets, ds.K));
-        RC(launch_walk(c, c->tbc.R, c->tb.p, je, (int)(lo * BR)));
+        RC(run_fill(c, c->tbc, kModeTb, fold, tasks, tickets, ds.K));
+        const size_t tbytes = table.size() * sizeof(void *);
+        if (tbytes > c->stage2.cap) return SW_EINVAL;
+        std::memcpy(c->stage2.p, table.data(), tbytes);
+        CU(cudaMemcpyAsync(c->misc.p, c->stage2.p, tbytes, cudaMemcpyHostToDevice, c->stream));
+        RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), I0, J0, nI, nJ, (int)BT, R));
         CU(cudaMemcpyAsync(c->stage3.p, c->walk.p, sizeof(WalkState), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 64, c->err.p, sizeof(int),
                            cudaMemcpyDeviceToHost, c->stream));
@@ -189,7 +203,9 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         std::memcpy(&w, c->stage3.p, sizeof(w));
         std::memcpy(&e, static_cast<char *>(c->stage3.p) + 64, sizeof(int));
         RC(map_kernel_error(e));
-        hi = lo - 1;
+        if (w.done != 0) break;
+        if (w.i == prev_i && w.j == prev_j && w.state == prev_state) return SW_ECUDA;   // no progress
+        prev_i = w.i; prev_j = w.j; prev_state = w.state;
     }
     if (w.done != 1) return SW_ECUDA;     // the walk must end at a zero cell or the border
 

@@ -52,7 +52,7 @@ struct sw_ctx {
     swgb::FillConfig tbc{8, 4};       // traceback recompute
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
-    swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, tb,
+    swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, tb,
         tbbnd, runs, walk, misc;
     swgb::HostBuf stage, stage2, stage3;
 };
@@ -65,8 +65,10 @@ int max_pos_score(const sw_scoring *sc);
 int stage_seq(sw_ctx *c, const uint8_t *p, int64_t len, DevBuf &buf, const uint8_t **dptr);
 int map_kernel_error(int e);
 int fill_rows_per_strip(const FillConfig &cfg);
-int launch_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const FillLaunch &L, int K, long long tickets);
-int run_fill(sw_ctx *c, const FillConfig &cfg, bool tb, const std::vector<FillTask> &tasks,
+bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
+int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
+                long long tickets);
+int run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const std::vector<FillTask> &tasks,
              long long tickets, int K);
 int upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s);
 int reset_err(sw_ctx *c);

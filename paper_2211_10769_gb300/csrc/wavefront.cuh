@@ -2,37 +2,42 @@
 // one matrix, all processing elements cooperate and pass border elements to
 // their neighbours).
 //
-// Layout of the work.  A "task" is a range of rows of one pair (sequence a
-// down the rows, b across the columns) swept over all of its columns.  It is
-// cut into strips of HC = W*32*R rows; one thread block computes one strip
-// at a time:
-//   * each of its W compute warps owns 32*R consecutive rows, each lane R of
-//     them, held in registers (H, H - open, E per row);
-//   * lanes form an anti-diagonal wavefront: at warp step s lane t computes
-//     column s - t, receiving the bottom H/F of lane t-1 for that column
-//     by warp shuffle;
-//   * warps hand their bottom row to the next warp through a shared-memory
-//     ring, advancing in phases of CH steps separated by one block barrier;
-//     warp w runs D = CH + 32 steps behind warp w-1, which is exactly what
-//     the ring needs;
-//   * an extra I/O warp moves the strip's top boundary row (H, F per column)
-//     from global memory into the ring and the strip's bottom row out to
-//     global memory, publishing its progress through a per-strip counter
-//     with release/acquire semantics; the next strip polls that counter
-//     (bounded spin) before reading.
-// Strips are claimed in order from a global ticket counter, so a strip only
-// ever waits on strips already held by running blocks.
+// A "task" is a rectangle of one pair: rows [0, rows) of its `a` slice
+// against columns [0, ncols) of its `b` slice, entered from a top boundary
+// row (H, F per column; the matrix border when null) and a left boundary
+// column (H, E per row; the matrix border when null).  It is cut into
+// strips of HC = W*32*R rows; one thread block computes one strip at a time.
 //
-// The substitution scores of the strip's rows are staged once per strip as
-// a query profile in shared memory: prof[c*HC + r] = S(a_r, c), int8, with
-// one extra padding residue c = K scoring -128 (used for columns outside
-// the matrix; rows beyond the task also score -128).
+//   * Each of the W compute warps owns 32*R consecutive rows, each lane R
+//     of them in registers.  Lanes form an anti-diagonal wavefront: at warp
+//     step s lane t computes column s - t and receives the bottom H / F of
+//     lane t-1 for that column by warp shuffle.
+//   * Warps hand their bottom row to the next warp through shared-memory
+//     rings guarded by acquire/release counters (no block barriers in the
+//     sweep); every wait is bounded.
+//   * A separate I/O warp streams the strip's top boundary row and the
+//     column residues into shared memory, ahead of warp 0, and drains the
+//     strip's bottom row to global memory, publishing how many columns are
+//     stored with st.release.gpu; the next strip's I/O warp reads that
+//     counter with ld.acquire.gpu.
+//   * Strips are claimed from a global ticket counter in order, so a strip
+//     only waits on strips already held by running blocks.
 //
-// Modes: score (TB = false) tracks, per lane, the best H and its first
-// column (then first row) and writes one end-cell candidate per strip;
-// traceback (TB = true) writes, for every cell, four decision bits
+// Cell update (R rows of one column).  With e <= o the vertical gap obeys
+//   F(i+1,j) = max(F(i,j) - e, X(i,j) - o),  X = max(0, H(i-1,j-1)+S, E)
+// because H = max(X, F) and F - o <= F - e; so the dependency from one row
+// to the next is a single max-add, and H = max(X, F), H - o = max(F - o,
+// X - o) follow off that chain.  Scores come from a per-strip query profile
+// in shared memory, prof[c*HC + r] = S(a_r, c) (int8, padding residue
+// c = K at -128), one vector load and one prmt per cell.
+//
+// Modes: score (TB = false) keeps, per lane, the best H with its first
+// column, then first row, and writes one end-cell candidate per strip; it
+// can also store the strip's bottom row as a checkpoint row and, every
+// `colck_every` columns, the (H, E) column as a checkpoint column.
+// Traceback (TB = true) writes, for every cell, four decision bits
 // {H source: 0 zero, 1 diagonal, 2 E, 3 F; E opened; F opened} packed R
-// nibbles per word, which a later walk follows.
+// nibbles per word, for the walk.
 #pragma once
 #include "sw_device.cuh"
 
@@ -40,19 +45,24 @@ namespace swgb {
 
 struct FillTask {
     const uint8_t *a;      // the task's rows: a[0 .. rows)
-    const uint8_t *b;      // columns b[0 .. ncols)
+    const uint8_t *b;      // the task's columns: b[0 .. ncols)
     int32_t rows;
     int32_t ncols;
     int32_t nstrips;
     int32_t scoring;       // index into the scoring table
     int64_t ticket0;       // global ticket of strip 0
-    const int2 *top;       // top boundary (H, F) per column, or null for the matrix border
+    const int2 *top;       // (H, F) per column of the row above, or null (matrix border)
+    const int2 *left;      // (H, E) per row of the column to the left, or null (matrix border)
+    const int2 *corner;    // H of the cell above-left in .x, or null (0)
     int2 *bnd;             // bottom rows of the strips: slot (strip % nslot) * ncols
     int32_t nslot;
-    int32_t ckpt_every;    // also copy every ckpt_every-th strip's bottom row to ckpt (0 = never)
+    int32_t ckpt_every;    // also copy every ckpt_every-th strip's bottom row to ckpt (0 = never);
+                           // only strips whose bottom row is inside the task: rows / (HC * ckpt_every) rows
     int2 *ckpt;            // checkpoint rows: ((strip+1)/ckpt_every - 1) * ncols
+    int2 *colck;           // checkpoint columns (H, E): (c/colck_every - 1) * colck_ld + row
+    int32_t colck_every;   // 0 = none; else store after every colck_every-th column
     int32_t row0;          // row index (0-based, in the whole pair) of the task's first row
-    int32_t pad_;
+    int64_t colck_ld;
     void *tb;              // traceback words, TB mode: [row group][tb_ld]
     int64_t tb_ld;
 };
@@ -79,41 +89,175 @@ __device__ __forceinline__ void load_profile(const int8_t *p, uint32_t (&w)[R / 
     if constexpr (R == 4) {
         w[0] = *reinterpret_cast<const uint32_t *>(p);
     } else if constexpr (R == 8) {
-        uint2 v = *reinterpret_cast<const uint2 *>(p);
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
         w[0] = v.x; w[1] = v.y;
     } else {
-        uint4 v = *reinterpret_cast<const uint4 *>(p);
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
         w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     }
 }
 
-template <int r>
-__device__ __forceinline__ int prof_score(const uint32_t *w) {
-    return sext8<r % 4>(w[r / 4]);
+__device__ __forceinline__ int score_byte(const uint32_t *w, int r) {
+    switch (r & 3) {            // r is a constant after unrolling: one prmt
+        case 0: return sext8<0>(w[r >> 2]);
+        case 1: return sext8<1>(w[r >> 2]);
+        case 2: return sext8<2>(w[r >> 2]);
+        default: return sext8<3>(w[r >> 2]);
+    }
 }
 
-template <int R, int W, bool TB>
-__global__ void __launch_bounds__((W + 1) * 32)
+__device__ __forceinline__ int lds_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void sts_release(int *p, int v) {
+    asm volatile("st.release.cta.shared.b32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+// Lane 0 waits until *ctr >= want (bounded); the result is broadcast.  false
+// on timeout or when the block is aborting.
+__device__ __forceinline__ bool warp_wait_geq(const int *ctr, int want, const volatile int *abort_flag,
+                                              long long limit, int *err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        long long it = 0;
+        while (lds_acquire(ctr) < want) {
+            if (*abort_flag) { ok = 0; break; }
+            if (++it > limit) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
+            __nanosleep(20);
+        }
+    }
+    __syncwarp();                       // orders the other lanes' reads after lane 0's acquire
+    return __shfl_sync(kFull, ok, 0) != 0;
+}
+
+enum FillMode { kModeScore = 0, kModeScoreCk = 1, kModeTb = 2 };
+
+constexpr int kCH = 16;       // steps between the warps' counter updates
+constexpr int kQS = 256;      // boundary-ring columns per channel
+constexpr int kQB = 1024;     // residue-ring columns
+constexpr int kIOB = 64;      // columns per I/O batch
+
+// Per-lane state of the sweep.  U = H - open and E of the lane's R rows at
+// the previous column; ub / fb the bottom row's U and F of the previous step
+// (shuffled to the next lane); udiag0 = U of the row above the first row at
+// the previous column (the first row's diagonal); the best U so far with
+// its column and row.
+template <int R>
+struct LaneState {
+    int U[R], E[R];
+    int ub, fb, udiag0;
+    int best, bj, br;
+    int cm;          // column maximum of the previous step
+    int pending;     // the previous step's column beat `best`; resolved at the next step
+    int next_ck;
+};
+
+// Record the previous step's improvement: best column j - 1 and its first row
+// reaching the maximum (U still holds that column).  Taken at the start of
+// a step, so the branch condition is ready long before it is needed.
+template <int R>
+__device__ __forceinline__ void resolve_pending(LaneState<R> &st, int jprev) {
+    if (st.pending) {
+        st.best = st.cm;
+        st.bj = jprev;
+        int rr = R - 1;
+#pragma unroll
+        for (int r = R - 1; r >= 0; --r) if (st.U[r] == st.cm) rr = r;
+        st.br = rr;
+        st.pending = 0;
+    }
+}
+
+// One wavefront step of one lane: column j = s - lane of its R rows.
+// CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
+// a sweep); the steady state skips those tests.
+template <int R, int MODE, bool FOLD, bool CHECK>
+__device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[R / 4], int2 top,
+                                          int s, int lane, int n, int go, int ge,
+                                          int2 *ring_out, typename TbWord<R>::T *tbw,
+                                          int2 *colck, long long colck_ld, int colck_every,
+                                          int grow, int rows)
+{
+    const int j = s - lane;
+    int uup = __shfl_up_sync(kFull, st.ub, 1);
+    int fup = __shfl_up_sync(kFull, st.fb, 1);
+    if (lane == 0) { uup = top.x; fup = top.y; }
+    if constexpr (MODE != kModeTb) resolve_pending(st, j - 1);
+    if (CHECK && (j < 0 || j >= n)) return;
+    int udiag = st.udiag0;
+    st.udiag0 = uup;
+    int f = __viaddmax_s32(fup, -ge, uup);                 // F of the first row
+    int fopen_ref = uup;                                   // H(i-1,j) - open
+    typename TbWord<R>::T word = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int sp = score_byte(pw, r);                        // S (+ open when folded)
+        if constexpr (!FOLD) sp += go;
+        const int uold = st.U[r];                          // H(i,j-1) - open
+        const int e = __viaddmax_s32(st.E[r], -ge, uold);
+        const int x = __viaddmax_s32_relu(udiag, sp, e);   // max(H(i-1,j-1) + S, E, 0)
+        const int xgo = x - go;
+        const int u = __viaddmax_s32(f, -go, xgo);         // H(i,j) - open
+        if constexpr (MODE == kModeTb) {
+            const int h = u + go, diag = udiag + sp;
+            const unsigned src = h == 0 ? 0u : (h == diag ? 1u : (h == e ? 2u : 3u));
+            const unsigned nib = src | (e == uold ? 4u : 0u) | (f == fopen_ref ? 8u : 0u);
+            word |= (typename TbWord<R>::T)nib << (4 * r);
+            fopen_ref = u;
+        }
+        st.E[r] = e;
+        udiag = uold;
+        st.U[r] = u;
+        if (r + 1 < R) f = __viaddmax_s32(f, -ge, xgo);    // F of the next row
+    }
+    st.ub = st.U[R - 1];
+    st.fb = f;
+    if (lane == 31) ring_out[j & (kQS - 1)] = make_int2(st.ub, st.fb);
+    if constexpr (MODE == kModeTb) {
+        tbw[j] = word;
+    } else {
+        int cm = st.U[0];
+#pragma unroll
+        for (int r = 1; r + 1 < R; r += 2) cm = __vimax3_s32(cm, st.U[r], st.U[r + 1]);
+        if constexpr (R % 2 == 0) cm = max(cm, st.U[R - 1]);
+        st.cm = cm;
+        st.pending = cm > st.best;
+        if constexpr (MODE == kModeScoreCk) {
+            if (j == st.next_ck) {
+                int2 *cc = colck + (size_t)((j + 1) / colck_every - 1) * (size_t)colck_ld;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (grow + r < rows) cc[r] = make_int2(st.U[r] + go, st.E[r]);
+                st.next_ck += colck_every;
+            }
+        }
+    }
+}
+
+template <int R, int W, int MODE, bool FOLD>
+__global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(R >= 16 ? 128 : 96)
 wavefront_kernel(const FillLaunch L)
 {
     constexpr int HC = W * 32 * R;
-    constexpr int CH = 16;
-    constexpr int D = CH + 32;
-    constexpr int QS = 64;
-    static_assert(QS >= 2 * CH + 1, "ring too small");
+    constexpr int CH = kCH, QS = kQS, QB = kQB, IOB = kIOB;
+    static_assert(QS >= 2 * IOB + 2 * CH + 64, "ring too small");
 
     extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC
-    __shared__ int2 chan[W + 1][QS];
+    __shared__ int2 ring[W + 1][QS];                 // channel k: producer k-1 (I/O for k=0), consumer k (I/O for k=W); (H - open, F)
+    __shared__ uint8_t bring[QB];
+    __shared__ int prod[W + 1];                      // columns available in channel k
+    __shared__ int cons[W + 1];                      // columns consumed from channel k
     __shared__ long long s_tk;
     __shared__ int s_task;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
     __shared__ int4 s_cand[W];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const bool io = (warp == W);
-
-    int H[R], U[R], E[R];
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -124,12 +268,13 @@ wavefront_kernel(const FillLaunch L)
             if (tk < L.total) {
                 int lo = 0, hi = L.ntasks - 1;               // last task with ticket0 <= tk
                 while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
+                    const int mid = (lo + hi + 1) >> 1;
                     if (L.tasks[mid].ticket0 <= tk) lo = mid; else hi = mid - 1;
                 }
                 s_task = lo;
             }
         }
+        if (threadIdx.x <= W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
         __syncthreads();
         const long long tk = s_tk;
         if (tk >= L.total) return;
@@ -139,170 +284,180 @@ wavefront_kernel(const FillLaunch L)
         const int strip = (int)(tk - T.ticket0);
         const int rbase = strip * HC;                   // first row of the strip within the task
         const int n = T.ncols;
-        const uint8_t *__restrict__ bseq = T.b;
 
-        // ---- query profile of the strip's rows
+        // ---- query profile of the strip's rows: S(a_r, c) (+ open when folded)
         for (int lr = threadIdx.x; lr < HC; lr += blockDim.x) {
             const int r = rbase + lr;
             const bool ok = r < T.rows;
             const int av = ok ? min((int)T.a[r], K - 1) : 0;
             for (int c = 0; c <= K; ++c)
-                prof[c * HC + lr] = (ok && c < K) ? SC.mat[av * K + c] : (int8_t)kPadScore;
-        }
-
-        // ---- per-lane state
-        int hb = 0, fb = kNeg, hprev = 0;
-        int best = 0, bj = -1, br = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) { H[r] = 0; U[r] = -go; E[r] = kNeg; }
-        const int lrow = (warp * 32 + lane) * R;            // first row of this lane within the strip
-        const int8_t *prow = prof + lrow;
-
-        // I/O helpers
-        auto load_cols = [&](int lo2, int hi2) -> bool {
-            if (hi2 <= lo2) return true;
-            if (strip == 0) {
-                for (int col = lo2 + lane; col < hi2; col += 32)
-                    chan[0][col & (QS - 1)] = T.top ? __ldcg(T.top + col) : make_int2(0, kNeg);
-                return true;
-            }
-            bool ok = true;
-            if (lane == 0) {
-                const int *pf = L.prog + (tk - 1);
-                long long it = 0;
-                while (ld_acquire(pf) < hi2) {
-                    if (++it > L.spin_limit || ld_volatile(L.err) != 0) {
-                        atomicCAS(L.err, 0, kErrTimeout);
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
-            if (!ok) return false;
-            const int2 *src = T.bnd + (size_t)((strip - 1) % T.nslot) * n;
-            for (int col = lo2 + lane; col < hi2; col += 32)
-                chan[0][col & (QS - 1)] = __ldcg(src + col);
-            return true;
-        };
-
-        if (io) {
-            if (!load_cols(0, min(n, CH))) s_abort = 1;
+                prof[c * HC + lr] = (ok && c < K) ? (int8_t)(SC.mat[av * K + c] + (FOLD ? go : 0))
+                                                  : (int8_t)kPadScore;
         }
         __syncthreads();
 
-        const int nphase = (n + 30 + (W - 1) * D) / CH + 2;
-        for (int p = 0; p < nphase && !s_abort; ++p) {
-            if (!io) {
-                const int s0 = p * CH - warp * D;
-#pragma unroll 2
-                for (int k = 0; k < CH; ++k) {
-                    const int s = s0 + k;
-                    if (s < 0 || s >= n + 31) continue;         // warp-uniform
-                    const int j = s - lane;
-                    const bool colok = (unsigned)j < (unsigned)n;
-                    int hup = __shfl_up_sync(kFull, hb, 1);
-                    int fup = __shfl_up_sync(kFull, fb, 1);
-                    if (lane == 0) {
-                        const int2 v = chan[warp][j & (QS - 1)];
-                        hup = v.x; fup = v.y;
+        if (io) {
+            // ================= I/O warp =================
+            int in_next = 0, out_next = 0;
+            long long idle = 0;
+            const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
+            int2 *dst = T.bnd + (size_t)(strip % T.nslot) * n;
+            // a checkpoint row only where the strip's bottom row lies inside the task
+            // (the last strip may be partial)
+            const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
+                            (long long)(strip + 1) * HC <= (long long)T.rows;
+            int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
+            const int *pprev = L.prog + (tk - 1);
+            int avail_prev = strip == 0 ? n : 0;
+            while (out_next < n) {
+                bool moved = false;
+                if (in_next < n) {
+                    // room in channel 0 (consumer: warp 0) and in the residue ring
+                    // (slowest reader: warp W-1, whose lane 31 is at column prod[W])
+                    const int room0 = lds_acquire(&cons[0]) + QS;
+                    const int roomb = lds_acquire(&prod[W]) + QB - 64;
+                    int target = min(n, min(in_next + IOB, min(room0, roomb)));
+                    if (target > in_next && strip > 0 && avail_prev < target) {
+                        int v = 0;
+                        if (lane == 0) v = ld_acquire(pprev);
+                        avail_prev = __shfl_sync(kFull, v, 0);
                     }
-                    const int c = colok ? min((int)bseq[j], K) : K;   // codes >= K are flagged by the validation kernel
-                    uint32_t pw[R / 4];
-                    load_profile<R>(prow + c * HC, pw);
-                    int hdiag = hprev;
-                    hprev = hup;
-                    int f = fup;
-                    int uu = hup - go;
-                    typename TbWord<R>::T word = 0;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        int sr;
-                        switch (r % 4) {
-                            case 0: sr = sext8<0>(pw[r / 4]); break;
-                            case 1: sr = sext8<1>(pw[r / 4]); break;
-                            case 2: sr = sext8<2>(pw[r / 4]); break;
-                            default: sr = sext8<3>(pw[r / 4]); break;
-                        }   // r is a constant after unrolling, so this folds to one prmt
-                        const int eopen = U[r];                    // H(i,j-1) - open
-                        const int e = __viaddmax_s32(E[r], -ge, eopen);
-                        const int fopen = uu;                      // H(i-1,j) - open
-                        f = __viaddmax_s32(f, -ge, fopen);
-                        const int hn = __viaddmax_s32_relu(hdiag, sr, max(e, f));
-                        if constexpr (TB) {
-                            const int diag = hdiag + sr;
-                            unsigned src = hn == 0 ? 0u : (hn == diag ? 1u : (hn == e ? 2u : 3u));
-                            unsigned nib = src | ((e == eopen) ? 4u : 0u) | ((f == fopen) ? 8u : 0u);
-                            word |= (typename TbWord<R>::T)nib << (4 * r);
+                    target = min(target, avail_prev);
+                    if (target > in_next) {
+                        for (int col = in_next + lane; col < target; col += 32) {
+                            const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
+                            ring[0][col & (QS - 1)] = make_int2(v.x - go, v.y);
+                            bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
                         }
-                        E[r] = e;
-                        hdiag = H[r];
-                        H[r] = hn;
-                        uu = hn - go;
-                        U[r] = uu;
-                    }
-                    hb = H[R - 1];
-                    fb = f;
-                    if (lane == 31 && colok) chan[warp + 1][j & (QS - 1)] = make_int2(hb, fb);
-                    if constexpr (TB) {
-                        if (colok) {
-                            auto *tbw = reinterpret_cast<typename TbWord<R>::T *>(T.tb);
-                            tbw[(size_t)((rbase + lrow) / R) * (size_t)T.tb_ld + j] = word;
-                        }
-                    } else {
-                        int cm = H[0];
-#pragma unroll
-                        for (int r = 1; r + 1 < R; r += 2) cm = __vimax3_s32(cm, H[r], H[r + 1]);
-                        if constexpr (R % 2 == 0) cm = max(cm, H[R - 1]);
-                        if (colok && cm > best) {
-                            best = cm;
-                            bj = j;
-                            int rr = R - 1;
-#pragma unroll
-                            for (int r = R - 1; r >= 0; --r) if (H[r] == cm) rr = r;
-                            br = rr;
-                        }
-                    }
-                }
-            } else {
-                // store the bottom-row columns warp W-1 produced in the previous phase
-                if (p >= 1) {
-                    const int lo = min(n, max(0, (p - 1) * CH - (W - 1) * D - 31));
-                    const int hi = min(n, max(0, p * CH - (W - 1) * D - 31));
-                    if (hi > lo) {
-                        int2 *dst = T.bnd + (size_t)(strip % T.nslot) * n;
-                        const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0;
-                        int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
-                        for (int col = lo + lane; col < hi; col += 32) {
-                            const int2 v = chan[W][col & (QS - 1)];
-                            dst[col] = v;
-                            if (ck) cdst[col] = v;
-                        }
-                        __threadfence();
                         __syncwarp();
-                        if (lane == 0) st_release(L.prog + tk, hi);
+                        if (lane == 0) sts_release(&prod[0], target);
+                        in_next = target;
+                        moved = true;
                     }
                 }
-                // fetch warp 0's top-boundary columns for the next phase
-                if (!load_cols(min(n, (p + 1) * CH), min(n, (p + 2) * CH))) s_abort = 1;
+                const int avail_out = lds_acquire(&prod[W]);
+                if (avail_out > out_next) {
+                    for (int col = out_next + lane; col < avail_out; col += 32) {
+                        const int2 u = ring[W][col & (QS - 1)];
+                        const int2 v = make_int2(u.x + go, u.y);
+                        dst[col] = v;
+                        if (ck) cdst[col] = v;
+                    }
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) {
+                        st_release(L.prog + tk, avail_out);
+                        sts_release(&cons[W], avail_out);
+                    }
+                    out_next = avail_out;
+                    moved = true;
+                }
+                if (moved) {
+                    idle = 0;
+                } else {
+                    if (s_abort) break;
+                    if (++idle > L.spin_limit) {
+                        if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
             }
-            __syncthreads();
-        }
-
-        if constexpr (!TB) {
-            // ---- end-cell candidate of the strip: best score, then first column, then first row
-            int cs = best, cj = bj + 1, ci = T.row0 + rbase + lrow + br + 1;
-            if (io || best <= 0 || rbase + lrow + br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
+        } else {
+            // ================= compute warp =================
+            const int lrow = (warp * 32 + lane) * R;        // first row of this lane within the strip
+            const int grow = rbase + lrow;                  // ... within the task
+            const int8_t *prow = prof + lrow;
+            LaneState<R> st;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const int os = __shfl_xor_sync(kFull, cs, off);
-                const int oj = __shfl_xor_sync(kFull, cj, off);
-                const int oi = __shfl_xor_sync(kFull, ci, off);
-                if (cand_better(os, oj, oi, cs, cj, ci)) { cs = os; cj = oj; ci = oi; }
+            for (int r = 0; r < R; ++r) {
+                int h0 = 0, e0 = kNeg;
+                if (T.left && grow + r < T.rows) { const int2 v = __ldcg(T.left + grow + r); h0 = v.x; e0 = v.y; }
+                st.U[r] = h0 - go; st.E[r] = e0;
             }
-            if (lane == 0 && !io) s_cand[warp] = make_int4(cs, ci, cj, 0);
-            __syncthreads();
+            st.ub = st.U[R - 1];
+            st.fb = kNeg;
+            // H of the row above this lane's first row, at the column left of the task
+            int hcorner;
+            if (grow == 0) hcorner = T.corner ? __ldcg(T.corner).x : 0;
+            else hcorner = (T.left && grow - 1 < T.rows) ? __ldcg(T.left + grow - 1).x : 0;
+            st.udiag0 = hcorner - go;
+            st.best = -go; st.bj = -1; st.br = 0; st.cm = -go; st.pending = 0;
+            const int colck_every = (MODE == kModeScoreCk) ? T.colck_every : 0;
+            st.next_ck = colck_every > 0 ? colck_every - 1 : 0x7fffffff;
+            int2 *colck = (MODE == kModeScoreCk && T.colck) ? T.colck + (T.row0 + grow) : nullptr;
+            typename TbWord<R>::T *tbw = nullptr;
+            if constexpr (MODE == kModeTb)
+                tbw = reinterpret_cast<typename TbWord<R>::T *>(T.tb) + (size_t)(grow / R) * (size_t)T.tb_ld;
+            int2 *rin = ring[warp];
+            int2 *rout = ring[warp + 1];
+
+            int seen_in = 0;
+            for (int s0 = 0; s0 < n + 31; s0 += CH) {
+                const int need_in = min(n, s0 + CH + 1);   // this chunk plus the next step's prefetch
+                if (need_in > seen_in) {
+                    if (!warp_wait_geq(&prod[warp], need_in, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
+                    seen_in = need_in;
+                }
+                const int out_hi = min(n, max(0, s0 + CH - 31));
+                if (out_hi > 0 && !warp_wait_geq(&cons[warp + 1], out_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
+                // inputs of the chunk's first step
+                int j = s0 - lane;
+                int c = ((unsigned)j < (unsigned)n) ? min((int)bring[j & (QB - 1)], K) : K;
+                uint32_t pw[R / 4];
+                load_profile<R>(prow + c * HC, pw);
+                int2 top = rin[s0 & (QS - 1)];
+                if (s0 >= 31 && s0 + CH + 1 <= n) {
+                    // steady state: every lane's column and the prefetched one are in [0, n)
+#pragma unroll 4
+                    for (int k = 0; k < CH; ++k) {
+                        const int s = s0 + k;
+                        const int cn = min((int)bring[(s + 1 - lane) & (QB - 1)], K);
+                        const int2 topn = rin[(s + 1) & (QS - 1)];
+                        uint32_t pwn[R / 4];
+                        load_profile<R>(prow + cn * HC, pwn);
+                        lane_step<R, MODE, FOLD, false>(st, pw, top, s, lane, n, go, ge, rout, tbw,
+                                                        colck, T.colck_ld, colck_every, grow, T.rows);
+#pragma unroll
+                        for (int q = 0; q < R / 4; ++q) pw[q] = pwn[q];
+                        top = topn;
+                    }
+                } else {
+                    for (int k = 0; k < CH; ++k) {
+                        const int s = s0 + k;
+                        if (s >= n + 31) break;
+                        lane_step<R, MODE, FOLD, true>(st, pw, top, s, lane, n, go, ge, rout, tbw,
+                                                       colck, T.colck_ld, colck_every, grow, T.rows);
+                        const int jn = s + 1 - lane;
+                        const int cn = ((unsigned)jn < (unsigned)n) ? min((int)bring[jn & (QB - 1)], K) : K;
+                        load_profile<R>(prow + cn * HC, pw);
+                        top = rin[(s + 1) & (QS - 1)];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    sts_release(&cons[warp], min(n, s0 + CH));
+                    if (out_hi > 0) sts_release(&prod[warp + 1], out_hi);
+                }
+            }
+
+            if constexpr (MODE != kModeTb) {
+                resolve_pending(st, n - 1);    // only lane 31 can hold one: its last step was column n - 1
+                int cs = st.best + go, cj = st.bj + 1, ci = T.row0 + grow + st.br + 1;
+                if (cs <= 0 || grow + st.br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const int os = __shfl_xor_sync(kFull, cs, off);
+                    const int oj = __shfl_xor_sync(kFull, cj, off);
+                    const int oi = __shfl_xor_sync(kFull, ci, off);
+                    if (cand_better(os, oj, oi, cs, cj, ci)) { cs = os; cj = oj; ci = oi; }
+                }
+                if (lane == 0) s_cand[warp] = make_int4(cs, ci, cj, 0);
+            }
+        }
+        __syncthreads();
+        if constexpr (MODE != kModeTb) {
             if (threadIdx.x == 0) {
                 int4 b = s_cand[0];
                 for (int w = 1; w < W; ++w) {
@@ -321,7 +476,7 @@ wavefront_kernel(const FillLaunch L)
 // out[k] = (score, a_end, b_end, 0) with a_end/b_end the 1-based cell
 // (= exclusive 0-based ends), all zero when the best score is 0.
 static __global__ void reduce_candidates_kernel(const FillTask *tasks, int ntasks, const int4 *cand,
-                                         int4 *out)
+                                                int4 *out)
 {
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;

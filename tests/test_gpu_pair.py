@@ -172,3 +172,49 @@ def test_invalid_arguments(ctx):
         ctx.encode("ACGT", "ACGN")
     # the context stays usable after errors
     assert ctx.score(a, a, sc.matrix, sc.gap_open, sc.gap_extend).score == 100
+
+
+def _long_gap_pair(seed, length, cut0, cut1, insert):
+    """A and B share A's sequence except that B lacks A[cut0:cut1] (a long
+    deletion) or, with insert=True, carries extra random bases there."""
+    A = W.uniform_dna(length, seed)
+    if insert:
+        extra = W.uniform_dna(cut1 - cut0, seed + 1)
+        B = np.concatenate([A[:cut0], extra, A[cut0:]])
+    else:
+        B = np.concatenate([A[:cut0], A[cut1:]])
+    B = W.mutate(B, 4, seed + 2, p_sub=0.08, p_indel=0.01)
+    return A, B
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_align_paths_cross_tiles(ctx, oracle_mod, case):
+    """Paths that cross many 1024 x 1024 tiles, including long vertical and
+    horizontal gap runs that leave the diagonal band of recomputed tiles."""
+    S = np.full((4, 4), -4, np.int8)
+    np.fill_diagonal(S, 5)
+    seed = W.BASE_SEED + 9400 + 10 * case
+    if case == 0:
+        A = W.uniform_dna(5000, seed)
+        B = W.mutate(A, 4, seed + 1, p_sub=0.1, p_indel=0.02)
+        o, e = 5, 2
+        S = W.dna_matrix()
+    elif case in (1, 2):
+        A, B = _long_gap_pair(seed, 6000, 2100, 3700, insert=(case == 2))
+        o, e = 20, 1
+    elif case == 3:
+        A, B = _long_gap_pair(seed, 4500, 1000, 3300, insert=False)
+        o, e = 10, 0
+    elif case == 4:
+        A = W.random_protein(3500, seed)
+        B = W.mutate(A, 20, seed + 1, p_sub=0.25, p_indel=0.03)
+        sc = W.protein_scoring()
+        S, o, e = sc.matrix, sc.gap_open, sc.gap_extend
+    else:
+        A, B = _long_gap_pair(seed, 3000, 600, 2800, insert=True)
+        o, e = 12, 1
+    want = oracle_mod.sw_align_ptr(A, B, S, o, e)
+    got = ctx.align(A, B, S, o, e)
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+        (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end)
+    assert got.cigar == want.cigar
