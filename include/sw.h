@@ -180,6 +180,35 @@ int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8
                      const sw_scoring *sc, sw_hit *out);
 
 /*
+ * Database of subject sequences for one-to-many search (paper Section 2.1,
+ * database similarity search; Section 3.2 searches UniProtKB/Swiss-Prot).
+ * residues holds all subjects back to back (codes, host or device memory),
+ * offsets (host memory, nseq + 1 entries, offsets[0] = 0, non-decreasing)
+ * delimits subject s = residues[offsets[s] .. offsets[s+1]).  The database
+ * is copied to the device of ctx and sorted by length there once; the
+ * caller's buffers are not retained.  nseq <= 2^30.  Codes are checked
+ * against the alphabet of each search (SW_EINVAL if one is too large).
+ */
+int sw_db_create(sw_ctx *ctx, const uint8_t *residues, const int64_t *offsets, int64_t nseq, sw_db **out);
+void sw_db_destroy(sw_db *db);
+
+/* Number of subjects of a database (-1 for NULL). */
+int64_t sw_db_size(const sw_db *db);
+
+/*
+ * Search the database with query q (length m, host or device memory):
+ * the local alignment score of q against every subject, and the k best
+ * hits (0 <= k <= 64) ordered by score descending, then subject index
+ * ascending; subjects with score 0 are ranked too.  hits (host, k entries)
+ * receives min(k, nseq) hits and *nhits their count.  all_scores, when not
+ * NULL, receives every subject's score (nseq int32, host or device memory).
+ * Scores are computed in packed 16-bit lanes; a subject whose score could
+ * saturate them is rescored exactly in 32 bits, so every score is exact.
+ */
+int sw_dbsearch(sw_ctx *ctx, const sw_db *db, const uint8_t *q, int64_t m, const sw_scoring *sc,
+                int32_t k, sw_dbhit *hits, int32_t *nhits, int32_t *all_scores);
+
+/*
  * Number of kernels this context has launched since it was created
  * (diagnostics: lets a caller count device launches per call).  Returns -1
  * for a null context.

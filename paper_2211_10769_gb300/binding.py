@@ -45,6 +45,10 @@ class _Alignment(ctypes.Structure):
                 ("cigar", ctypes.c_void_p), ("cigar_len", ctypes.c_int64)]
 
 
+class _DbHit(ctypes.Structure):
+    _fields_ = [("subject", ctypes.c_int64), ("score", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -70,6 +74,13 @@ def load():
     lib.sw_alignment_free.restype = None
     lib.sw_ctx_launches.argtypes = [vp]
     lib.sw_ctx_launches.restype = i64
+    lib.sw_db_create.argtypes = [vp, vp, vp, i64, ctypes.POINTER(vp)]
+    lib.sw_db_destroy.argtypes = [vp]
+    lib.sw_db_destroy.restype = None
+    lib.sw_db_size.argtypes = [vp]
+    lib.sw_db_size.restype = i64
+    lib.sw_dbsearch.argtypes = [vp, vp, vp, i64, ctypes.POINTER(_Scoring), ctypes.c_int32,
+                                ctypes.POINTER(_DbHit), ctypes.POINTER(ctypes.c_int32), vp]
     _lib = lib
     return lib
 
@@ -182,6 +193,50 @@ class Context:
         finally:
             self._lib.sw_alignment_free(ctypes.byref(aln))
         return Alignment(aln.score, aln.a_begin, aln.a_end, aln.b_begin, aln.b_end, cig)
+
+
+class Database:
+    """A device-resident database (sw_db) built from residues + offsets."""
+
+    def __init__(self, ctx: Context, residues, offsets):
+        self._lib = load()
+        self.ctx = ctx
+        res = np.ascontiguousarray(np.asarray(residues, dtype=np.uint8))
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        h = ctypes.c_void_p()
+        _check(self._lib.sw_db_create(ctx.handle, res.ctypes.data if res.size else None,
+                                      off.ctypes.data, len(off) - 1, ctypes.byref(h)), "sw_db_create")
+        self.handle = h
+        self.nseq = len(off) - 1
+
+    def close(self):
+        if self.handle:
+            self._lib.sw_db_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def search(self, q, matrix, gap_open: int, gap_extend: int, k: int = 20, all_scores: bool = False,
+               scores_out=None):
+        """(hits, scores): hits = [(subject, score)] best first; scores = int32 array or None.
+        scores_out may be a preallocated int32 numpy array or torch CUDA tensor."""
+        pq, m, kq = _seq(q)
+        sc, keep = _scoring(matrix, gap_open, gap_extend)
+        hits = (_DbHit * max(1, k))()
+        nh = ctypes.c_int32()
+        out = scores_out
+        if out is None and all_scores:
+            out = np.zeros(self.nseq, dtype=np.int32)
+        ptr = None
+        if out is not None:
+            ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        _check(self._lib.sw_dbsearch(self.ctx.handle, self.handle, pq, m, ctypes.byref(sc), int(k),
+                                     hits, ctypes.byref(nh), ptr), "sw_dbsearch")
+        return [(int(hits[i].subject), int(hits[i].score)) for i in range(nh.value)], out
 
 
 PROBE_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,

@@ -1,0 +1,281 @@
+// dbsearch.cuh -- inter-task database search (paper Section 2.1: many
+// matrices at once, no communication between processing elements), packed
+// 16-bit lanes with exact 32-bit rescoring of saturating subjects, and the
+// top-k selection of the hits.
+//
+// One warp aligns the query against two database subjects at once: the low
+// 16 bits of every register belong to subject A, the high 16 bits to
+// subject B (the database is sorted by length, so the two have nearly the
+// same length).  The query runs down the warp: lane t owns R query rows of
+// the current pass of 32*R rows; lanes form an anti-diagonal wavefront over
+// the subjects' columns exactly as in the pairwise fill (bottom H / F to the
+// next lane by shuffle), and longer queries take several passes, the bottom
+// row of one pass feeding the next through a per-warp boundary row in
+// global memory.  The query profile (int8, S + open, all passes) sits in
+// shared memory; the two residues' score bytes are merged into one packed
+// register with a single prmt.  The cell update is the pairwise one in
+// __viaddmax_s16x2 / __viaddmax_s16x2_relu form.
+//
+// Exactness of 16-bit lanes: every H value is exact while all H values of
+// the subject stay <= T = 32767 - max(S) (the largest intermediate is
+// H + S, E and F never drop below -open - extend - 16384).  The first cell
+// whose H exceeds T is still exact and raises the running maximum above T,
+// so a subject whose maximum exceeds T is flagged and rescored in 32 bits;
+// all other scores are exact.
+#pragma once
+#include "sw_device.cuh"
+
+namespace swgb {
+
+constexpr int kNeg16 = -16384;
+
+struct DbJob {
+    const uint8_t *q;          // query codes (device)
+    int32_t m;                 // query length
+    int32_t scoring;           // index into the scoring table
+    int32_t pair0, pair1;      // pairs [pair0, pair1) of the sorted database
+    int32_t *scores;           // per subject (original index): score, or -1 when flagged
+    int32_t *ovf;              // flagged subject ids
+    int32_t *novf;             // their count
+    int32_t *next_pair;        // work counter (zeroed before launch)
+};
+
+struct DbView {
+    const uint8_t *res;        // all residues
+    const int64_t *off;        // subject s = res[off[s] .. off[s+1])
+    const int32_t *pairs;      // pair p = subjects pairs[2p], pairs[2p+1] (-1 = none)
+    int32_t npairs;
+    int32_t maxlen;
+};
+
+__device__ __forceinline__ unsigned pack2(int lo, int hi) {
+    return (unsigned)(lo & 0xffff) | ((unsigned)hi << 16);
+}
+
+__device__ __forceinline__ int lo16(unsigned v) { return (int)(short)(v & 0xffff); }
+__device__ __forceinline__ int hi16(unsigned v) { return (int)(short)(v >> 16); }
+
+// Packed profile pair for row byte k of two profile words (sign-extended bytes).
+template <int k>
+__device__ __forceinline__ unsigned merge_bytes(uint32_t a, uint32_t b) {
+    constexpr uint32_t sel = k | ((8 | k) << 4) | ((4 + k) << 8) | ((8 | (4 + k)) << 12);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "n"(sel));
+    return d;
+}
+
+__device__ __forceinline__ unsigned merge_row(const uint32_t *wa, const uint32_t *wb, int r) {
+    switch (r & 3) {                 // r is a constant after unrolling
+        case 0: return merge_bytes<0>(wa[r >> 2], wb[r >> 2]);
+        case 1: return merge_bytes<1>(wa[r >> 2], wb[r >> 2]);
+        case 2: return merge_bytes<2>(wa[r >> 2], wb[r >> 2]);
+        default: return merge_bytes<3>(wa[r >> 2], wb[r >> 2]);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R / 4]) {
+    if constexpr (R == 4) {
+        w[0] = *reinterpret_cast<const uint32_t *>(p);
+    } else if constexpr (R == 8) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        w[0] = v.x; w[1] = v.y;
+    } else {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+}
+
+// grid: (blocks, jobs); block: W warps.  Dynamic shared memory: the query
+// profile, (K + 1) * mpad bytes, mpad = passes * 32 * R.
+template <int R, int W>
+__global__ void __launch_bounds__(W * 32)
+db_s16x2_kernel(const DbJob *__restrict__ jobs, const DbView D, const DevScoring *__restrict__ scorings,
+                uint2 *__restrict__ scratch)
+{
+    extern __shared__ __align__(16) int8_t prof[];
+    const DbJob &J = jobs[blockIdx.y];
+    const DevScoring &SC = scorings[J.scoring];
+    const int K = SC.K, go = SC.go, ge = SC.ge;
+    const int m = J.m;
+    constexpr int ROWS = 32 * R;
+    const int passes = (m + ROWS - 1) / ROWS;
+    const int mpad = passes * ROWS;
+    for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
+        const bool ok = i < m;
+        const int qc = ok ? min((int)J.q[i], K - 1) : 0;
+        for (int c = 0; c <= K; ++c)
+            prof[c * mpad + i] = (ok && c < K) ? (int8_t)(SC.mat[qc * K + c] + go) : (int8_t)kPadScore;
+    }
+    __syncthreads();
+
+    int maxs = 0;
+    for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
+    const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.y * gridDim.x + blockIdx.x) * W + (threadIdx.x >> 5);
+    uint2 *bnd = scratch + (size_t)gwarp * (size_t)D.maxlen;
+    const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
+    const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
+
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(J.next_pair, 1) + J.pair0;
+        p = __shfl_sync(kFull, p, 0);
+        if (p >= J.pair1) break;
+        const int sa = D.pairs[2 * p], sb = D.pairs[2 * p + 1];
+        const uint8_t *ra = D.res + D.off[sa];
+        const int na = (int)(D.off[sa + 1] - D.off[sa]);
+        const uint8_t *rb = sb >= 0 ? D.res + D.off[sb] : ra;
+        const int nb = sb >= 0 ? (int)(D.off[sb + 1] - D.off[sb]) : 0;
+        const int n = max(na, nb);
+        unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
+        for (int pass = 0; pass < passes; ++pass) {
+            const int8_t *prow = prof + pass * ROWS + lane * R;
+            unsigned U[R], E[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { U[r] = ngo2; E[r] = neg2; }
+            unsigned ub = ngo2, fb = neg2, udiag0 = ngo2;
+            const bool last = pass + 1 == passes;
+            // prefetched residues of this lane's column
+            int j = -lane;
+            int ca = (j >= 0 && j < na) ? ra[j] : K;
+            int cb = (j >= 0 && j < nb) ? rb[j] : K;
+            uint2 topv = (pass > 0 && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
+            for (int s = 0; s < n + 31; ++s) {
+                j = s - lane;
+                unsigned uup = __shfl_up_sync(kFull, ub, 1);
+                unsigned fup = __shfl_up_sync(kFull, fb, 1);
+                if (lane == 0) { uup = topv.x; fup = topv.y; }
+                const int jn = j + 1;
+                const int can = (jn >= 0 && jn < na) ? ra[jn] : K;
+                const int cbn = (jn >= 0 && jn < nb) ? rb[jn] : K;
+                uint2 topn = make_uint2(ngo2, neg2);
+                if (pass > 0 && s + 1 < n) topn = bnd[s + 1];
+                if (j >= 0 && j < n) {
+                    uint32_t wa[R / 4], wb[R / 4];
+                    load_prof_words<R>(prow + min(ca, K) * mpad, wa);
+                    load_prof_words<R>(prow + min(cb, K) * mpad, wb);
+                    unsigned udiag = udiag0;
+                    udiag0 = uup;
+                    unsigned f = __viaddmax_s16x2(fup, nge2, uup);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const unsigned sp = merge_row(wa, wb, r);
+                        const unsigned uold = U[r];
+                        const unsigned e = __viaddmax_s16x2(E[r], nge2, uold);
+                        const unsigned x = __viaddmax_s16x2_relu(udiag, sp, e);
+                        const unsigned xgo = __viaddmax_s16x2(x, ngo2, neg2);   // x - open
+                        const unsigned u = __viaddmax_s16x2(f, ngo2, xgo);      // H - open
+                        E[r] = e;
+                        udiag = uold;
+                        U[r] = u;
+                        if (r + 1 < R) f = __viaddmax_s16x2(f, nge2, xgo);
+                    }
+                    ub = U[R - 1];
+                    fb = f;
+#pragma unroll
+                    for (int r = 0; r + 1 < R; r += 2) cmax = __vimax3_s16x2(cmax, U[r], U[r + 1]);
+                    if (!last && lane == 31) bnd[j] = make_uint2(ub, fb);
+                }
+                ca = can;
+                cb = cbn;
+                topv = topn;
+            }
+            __syncwarp();
+        }
+        // warp maximum of each half
+        int ma = lo16(cmax), mb = hi16(cmax);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ma = max(ma, __shfl_xor_sync(kFull, ma, off));
+            mb = max(mb, __shfl_xor_sync(kFull, mb, off));
+        }
+        if (lane == 0) {
+            const int outs[2] = {sa, sb};
+            const int mx[2] = {ma, mb};
+            for (int h = 0; h < 2; ++h) {
+                const int s = outs[h];
+                if (s < 0) continue;
+                if (mx[h] > tmax_u) {
+                    J.scores[s] = -1;
+                    const int slot = atomicAdd(J.novf, 1);
+                    J.ovf[slot] = s;
+                } else {
+                    J.scores[s] = max(0, mx[h] + go);
+                }
+            }
+        }
+    }
+}
+
+// Write rescored (int32) results into the score array: scores[subject[k]] = res[k].x.
+static __global__ void scatter_scores_kernel(const int32_t *subject, const int4 *res, int count,
+                                             int32_t *scores) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) scores[subject[k]] = res[k].x;
+}
+
+// ---- top-k: key = (score << 32) | (0xffffffff - subject), larger is better
+__device__ __forceinline__ unsigned long long topk_key(int score, int s) {
+    return ((unsigned long long)(unsigned)score << 32) | (unsigned long long)(0xffffffffu - (unsigned)s);
+}
+
+// Block-wide top-k by k rounds of arg-max over a chunk held in shared
+// memory.  Phase 1: every block takes TOPK_CHUNK keys and writes its k
+// best; phase 2: one block does the same over all block winners.
+constexpr int kTopkThreads = 256;
+constexpr int kTopkChunk = 2048;
+
+__device__ void block_topk(unsigned long long *keys, int count, int k, unsigned long long *out) {
+    __shared__ unsigned long long red[kTopkThreads / 32];
+    __shared__ int redi[kTopkThreads / 32];
+    for (int it = 0; it < k; ++it) {
+        unsigned long long best = 0;
+        int bi = -1;
+        for (int i = threadIdx.x; i < count; i += blockDim.x)
+            if (bi < 0 || keys[i] > best) { best = keys[i]; bi = i; }
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
+            const int oi = __shfl_xor_sync(kFull, bi, off);
+            if (ob > best || (bi < 0 && oi >= 0)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = best; redi[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = 0;
+            int i0 = -1;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                if (redi[w] >= 0 && (red[w] > b || i0 < 0)) { b = red[w]; i0 = redi[w]; }
+            out[it] = i0 >= 0 ? b : 0;
+            if (i0 >= 0) keys[i0] = 0;          // taken
+        }
+        __syncthreads();
+    }
+}
+
+static __global__ void __launch_bounds__(kTopkThreads)
+topk_phase1_kernel(const int32_t *scores, int nseq, int k, unsigned long long *winners) {
+    __shared__ unsigned long long keys[kTopkChunk];
+    const int base = blockIdx.x * kTopkChunk;
+    const int cnt = min(kTopkChunk, nseq - base);
+    for (int i = threadIdx.x; i < kTopkChunk; i += blockDim.x)
+        keys[i] = i < cnt ? topk_key(max(scores[base + i], 0), base + i) : 0;
+    __syncthreads();
+    block_topk(keys, cnt, k, winners + (size_t)blockIdx.x * k);
+}
+
+static __global__ void __launch_bounds__(kTopkThreads)
+topk_phase2_kernel(const unsigned long long *winners, int count, int k, int2 *out) {
+    extern __shared__ unsigned long long keys2[];
+    for (int i = threadIdx.x; i < count; i += blockDim.x) keys2[i] = winners[i];
+    __syncthreads();
+    __shared__ unsigned long long best[64];
+    block_topk(keys2, count, k, best);
+    if (threadIdx.x < k) {
+        const unsigned long long b = best[threadIdx.x];
+        out[threadIdx.x] = make_int2((int)(0xffffffffu - (unsigned)(b & 0xffffffffu)), (int)(b >> 32));
+    }
+}
+
+}  // namespace swgb

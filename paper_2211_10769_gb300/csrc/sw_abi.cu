@@ -274,7 +274,7 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
         return SW_ECUDA;
     }
     int rc = c->err.ensure(256);
-    if (!rc) rc = c->stage3.ensure(256);
+    if (!rc) rc = c->stage3.ensure(4096);
     if (rc) { delete c; return rc; }
     if (cudaMemsetAsync(c->err.p, 0, 256, c->stream) != cudaSuccess) {
         cudaGetLastError();

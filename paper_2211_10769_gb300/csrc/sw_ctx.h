@@ -53,7 +53,7 @@ struct sw_ctx {
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
     swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, tb,
-        tbbnd, runs, walk, misc;
+        tbbnd, runs, walk, misc, dbscratch, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
 };
 
@@ -74,5 +74,9 @@ int upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s);
 int reset_err(sw_ctx *c);
 int validate_codes(sw_ctx *c, const uint8_t *d, int64_t len, int K);
 int read_err(sw_ctx *c, int *e);
+// database search pieces shared with the serving loop
+int db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
+                 int32_t *dscores);
+int db_topk(sw_ctx *c, const int32_t *dscores, int64_t nseq, int k, int2 *dout);
 
 }  // namespace swgb

@@ -1,0 +1,302 @@
+// sw_dbsearch.cu -- database search (paper Section 2.1, one-to-many,
+// inter-task): device-resident database, packed 16-bit search with exact
+// 32-bit rescoring of saturating subjects, top-k hits.
+#include "sw.h"
+#include "sw_ctx.h"
+#include "dbsearch.cuh"
+#include "wavefront.cuh"
+#include "aux_kernels.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+using namespace swgb;
+
+#define CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; } } while (0)
+#define RC(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+struct sw_db {
+    int device = 0;
+    int64_t nseq = 0;
+    int32_t npairs = 0;
+    int32_t maxlen = 0;
+    int32_t max_code = -1;
+    std::vector<int64_t> off;           // host copy of the offsets
+    DevBuf res, doff, pairs;
+};
+
+namespace {
+
+static __global__ void max_code_kernel(const uint8_t *s, long long len, int *out) {
+    int mx = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += stride)
+        mx = max(mx, (int)s[k]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+constexpr long long kMaxProfileSmem = 200 * 1024;
+
+template <int R, int W>
+int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, const DbView &D, int K, int m, int *grid_out) {
+    auto kern = db_s16x2_kernel<R, W>;
+    constexpr int ROWS = 32 * R;
+    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
+    const size_t smem = (size_t)(K + 1) * (size_t)mpad;
+    if ((long long)smem > kMaxProfileSmem) return SW_ERANGE;
+    static int attr_set[64] = {0};
+    if (c->device < 64 && !attr_set[c->device]) {
+        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxProfileSmem));
+        attr_set[c->device] = 1;
+    }
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, W * 32, smem));
+    if (occ < 1) return SW_ECUDA;
+    const int gx = std::max(1, std::min(occ * c->nsm, (D.npairs + W - 1) / W));
+    // boundary rows: one per warp
+    RC(c->dbscratch.ensure((size_t)gx * njobs * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    dim3 grid((unsigned)gx, (unsigned)njobs);
+    kern<<<grid, W * 32, smem, c->stream>>>(jobs, D, static_cast<const DevScoring *>(c->scorings.p),
+                                           static_cast<uint2 *>(c->dbscratch.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    if (grid_out) *grid_out = gx;
+    return SW_OK;
+}
+
+// Tile shape by query length: the whole profile must sit in shared memory;
+// long queries use one block of 32 warps per SM.
+int launch_db_auto(sw_ctx *c, const DbJob *jobs, int njobs, const DbView &D, int K, int m) {
+    const long long prof8 = (long long)(K + 1) * (((m + 255) / 256) * 256);
+    if (prof8 > 96 * 1024) return launch_db<8, 32>(c, jobs, njobs, D, K, m, nullptr);
+    if (m >= 1024) return launch_db<16, 8>(c, jobs, njobs, D, K, m, nullptr);
+    return launch_db<8, 8>(c, jobs, njobs, D, K, m, nullptr);
+}
+
+}  // namespace
+
+extern "C" int sw_db_create(sw_ctx *c, const uint8_t *residues, const int64_t *offsets, int64_t nseq,
+                            sw_db **out) {
+    if (!c || !out || !offsets || nseq < 0 || nseq > (int64_t)1 << 30) return SW_EINVAL;
+    if (offsets[0] != 0) return SW_EINVAL;
+    for (int64_t s = 0; s < nseq; ++s) {
+        if (offsets[s + 1] < offsets[s]) return SW_EINVAL;
+        if (offsets[s + 1] - offsets[s] > SW_MAX_LEN) return SW_ERANGE;
+    }
+    const int64_t total = offsets[nseq];
+    if (total > 0 && !residues) return SW_EINVAL;
+    DeviceGuard g(c->device);
+    sw_db *db = new (std::nothrow) sw_db();
+    if (!db) return SW_ENOMEM;
+    db->device = c->device;
+    db->nseq = nseq;
+    db->off.assign(offsets, offsets + nseq + 1);
+    int rc = db->res.ensure((size_t)total + 16);
+    if (!rc) rc = db->doff.ensure((size_t)(nseq + 1) * sizeof(int64_t));
+    if (rc) { delete db; return rc; }
+    // length-sorted pairs, longest first (ties by index)
+    std::vector<int32_t> order((size_t)nseq);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+    });
+    db->npairs = (int32_t)((nseq + 1) / 2);
+    std::vector<int32_t> pairs((size_t)db->npairs * 2, -1);
+    for (int64_t k = 0; k < nseq; ++k) pairs[(size_t)k] = order[(size_t)k];
+    int64_t maxlen = 0;
+    for (int64_t s = 0; s < nseq; ++s) maxlen = std::max(maxlen, offsets[s + 1] - offsets[s]);
+    db->maxlen = (int32_t)maxlen;
+    rc = db->pairs.ensure(std::max<size_t>(1, pairs.size()) * sizeof(int32_t));
+    if (rc) { delete db; return rc; }
+    const cudaMemcpyKind kind = is_device_ptr(residues) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    bool ok = true;
+    if (total > 0) ok &= cudaMemcpyAsync(db->res.p, residues, (size_t)total, kind, c->stream) == cudaSuccess;
+    ok &= cudaMemcpyAsync(db->doff.p, offsets, (size_t)(nseq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (!pairs.empty())
+        ok &= cudaMemcpyAsync(db->pairs.p, pairs.data(), pairs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    // largest residue code, checked against the alphabet at search time
+    ok &= c->misc.ensure(sizeof(int)) == SW_OK;
+    ok &= cudaMemsetAsync(c->misc.p, 0, sizeof(int), c->stream) == cudaSuccess;
+    if (ok && total > 0) {
+        max_code_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 8LL * c->nsm), 256, 0, c->stream>>>(
+            static_cast<const uint8_t *>(db->res.p), total, static_cast<int *>(c->misc.p));
+        ok &= cudaGetLastError() == cudaSuccess;
+        ++c->launches;
+    }
+    int mc = 0;
+    ok &= cudaMemcpyAsync(&mc, c->misc.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) == cudaSuccess;
+    ok &= cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); delete db; return SW_ECUDA; }
+    db->max_code = total > 0 ? mc : -1;
+    *out = db;
+    return SW_OK;
+}
+
+extern "C" void sw_db_destroy(sw_db *db) {
+    if (!db) return;
+    DeviceGuard g(db->device);
+    delete db;
+}
+
+extern "C" int64_t sw_db_size(const sw_db *db) { return db ? db->nseq : -1; }
+
+// Score every subject of the database against query q (device array
+// scores, int32 per subject), flagged subjects rescored exactly.
+int swgb::db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
+                       int32_t *dscores) {
+    const int K = ds.K;
+    RC(c->dbovf.ensure((size_t)std::max<int64_t>(1, db->nseq) * sizeof(int32_t)));
+    RC(c->dbjob.ensure(sizeof(DbJob) + 64));
+    int32_t *novf = reinterpret_cast<int32_t *>(static_cast<char *>(c->dbjob.p) + sizeof(DbJob));
+    int32_t *next = novf + 1;
+    CU(cudaMemsetAsync(novf, 0, 2 * sizeof(int32_t), c->stream));
+    DbJob job;
+    job.q = dq; job.m = (int32_t)m; job.scoring = 0;
+    job.pair0 = 0; job.pair1 = db->npairs;
+    job.scores = dscores;
+    job.ovf = static_cast<int32_t *>(c->dbovf.p);
+    job.novf = novf; job.next_pair = next;
+    RC(c->stage.ensure(sizeof(DbJob)));
+    std::memcpy(c->stage.p, &job, sizeof(job));
+    CU(cudaMemcpyAsync(c->dbjob.p, c->stage.p, sizeof(job), cudaMemcpyHostToDevice, c->stream));
+    DbView D;
+    D.res = static_cast<const uint8_t *>(db->res.p);
+    D.off = static_cast<const int64_t *>(db->doff.p);
+    D.pairs = static_cast<const int32_t *>(db->pairs.p);
+    D.npairs = db->npairs;
+    D.maxlen = db->maxlen;
+    int32_t nflag = 0;
+    std::vector<int32_t> flagged;
+    const bool packed_ok = fold_open(ds) && ds.go <= 16000 && ds.ge <= 16000;
+    int rc = packed_ok ? launch_db_auto(c, static_cast<const DbJob *>(c->dbjob.p), 1, D, K, (int)m) : SW_ERANGE;
+    if (rc == SW_ERANGE) {
+        // the packed kernel cannot take this query / scoring: score every subject in int32
+        flagged.resize((size_t)db->nseq);
+        std::iota(flagged.begin(), flagged.end(), 0);
+    } else {
+        RC(rc);
+        CU(cudaMemcpyAsync(c->stage3.p, novf, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        std::memcpy(&nflag, c->stage3.p, sizeof(int32_t));
+        if (nflag > 0) {
+            flagged.resize((size_t)nflag);
+            CU(cudaMemcpy(flagged.data(), c->dbovf.p, (size_t)nflag * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+    }
+    if (flagged.empty()) return SW_OK;
+    // exact rescoring: one int32 wavefront task per flagged subject (query down the rows)
+    const int HC = fill_rows_per_strip(c->fwd);
+    std::vector<FillTask> tasks;
+    tasks.reserve(flagged.size());
+    long long tickets = 0;
+    size_t bnd_need = 0;
+    for (int32_t s : flagged) {
+        const int64_t n = db->off[(size_t)s + 1] - db->off[(size_t)s];
+        const int ns = (int)((m + HC - 1) / HC);
+        bnd_need += (size_t)std::min(ns, 2) * (size_t)std::max<int64_t>(n, 1) * sizeof(int2);
+    }
+    RC(c->tbbnd.ensure(bnd_need));
+    size_t boff = 0;
+    for (int32_t s : flagged) {
+        FillTask u{};
+        const int64_t n = db->off[(size_t)s + 1] - db->off[(size_t)s];
+        u.a = dq; u.rows = (int32_t)m;
+        u.b = static_cast<const uint8_t *>(db->res.p) + db->off[(size_t)s];
+        u.ncols = (int32_t)n;
+        u.nstrips = (int32_t)((m + HC - 1) / HC);
+        u.scoring = 0;
+        u.ticket0 = tickets;
+        u.nslot = std::min(u.nstrips, 2);
+        u.bnd = reinterpret_cast<int2 *>(static_cast<char *>(c->tbbnd.p) + boff);
+        boff += (size_t)u.nslot * (size_t)std::max<int64_t>(n, 1) * sizeof(int2);
+        tickets += n > 0 ? u.nstrips : 0;
+        if (n == 0) { u.nstrips = 0; }
+        tasks.push_back(u);
+    }
+    RC(run_fill(c, c->fwd, kModeScore, fold_open(ds), tasks, tickets, K));
+    const int nt = (int)tasks.size();
+    RC(c->result.ensure((size_t)nt * sizeof(int4)));
+    reduce_candidates_kernel<<<(nt + 7) / 8, 256, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), nt,
+                                                                  static_cast<const int4 *>(c->cand.p),
+                                                                  static_cast<int4 *>(c->result.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    RC(c->dbovf.ensure((size_t)nt * sizeof(int32_t)));
+    CU(cudaMemcpyAsync(c->dbovf.p, flagged.data(), (size_t)nt * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    scatter_scores_kernel<<<(nt + 255) / 256, 256, 0, c->stream>>>(static_cast<const int32_t *>(c->dbovf.p),
+                                                                   static_cast<const int4 *>(c->result.p), nt, dscores);
+    CU(cudaGetLastError());
+    ++c->launches;
+    CU(cudaStreamSynchronize(c->stream));      // flagged is host memory used by the copy above
+    return SW_OK;
+}
+
+// Top-k of a device score array: (subject, score) pairs, score descending,
+// subject ascending.
+int swgb::db_topk(sw_ctx *c, const int32_t *dscores, int64_t nseq, int k, int2 *dout) {
+    const int nb = (int)((nseq + kTopkChunk - 1) / kTopkChunk);
+    RC(c->topk.ensure((size_t)std::max(1, nb) * k * sizeof(unsigned long long)));
+    topk_phase1_kernel<<<nb, kTopkThreads, 0, c->stream>>>(dscores, (int)nseq, k,
+                                                           static_cast<unsigned long long *>(c->topk.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    const size_t smem = (size_t)nb * k * sizeof(unsigned long long);
+    static int attr_set = 0;
+    if (!attr_set) {
+        CU(cudaFuncSetAttribute(topk_phase2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set = 1;
+    }
+    if (smem > 200 * 1024) return SW_ERANGE;
+    topk_phase2_kernel<<<1, kTopkThreads, smem, c->stream>>>(static_cast<const unsigned long long *>(c->topk.p),
+                                                             nb * k, k, dout);
+    CU(cudaGetLastError());
+    ++c->launches;
+    return SW_OK;
+}
+
+extern "C" int sw_dbsearch(sw_ctx *c, const sw_db *db, const uint8_t *q, int64_t m, const sw_scoring *sc,
+                           int32_t k, sw_dbhit *hits, int32_t *nhits, int32_t *all_scores) {
+    if (!c || !db || !nhits || k < 0 || k > 64 || (k > 0 && !hits)) return SW_EINVAL;
+    if (db->device != c->device) return SW_EINVAL;
+    DevScoring ds;
+    RC(check_scoring(sc, &ds));
+    if (m < 0 || (m > 0 && !q)) return SW_EINVAL;
+    if (m > SW_MAX_LEN) return SW_ERANGE;
+    if (db->max_code >= ds.K) return SW_EINVAL;
+    if ((double)std::min<int64_t>(m, db->maxlen) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    DeviceGuard g(c->device);
+    const int64_t nseq = db->nseq;
+    RC(c->dbscores.ensure((size_t)std::max<int64_t>(1, nseq) * sizeof(int32_t)));
+    int32_t *dscores = static_cast<int32_t *>(c->dbscores.p);
+    if (nseq > 0) CU(cudaMemsetAsync(dscores, 0, (size_t)nseq * sizeof(int32_t), c->stream));
+    if (m > 0 && nseq > 0) {
+        const uint8_t *dq;
+        RC(stage_seq(c, q, m, c->seq_a, &dq));
+        RC(reset_err(c));
+        RC(validate_codes(c, dq, m, ds.K));
+        RC(upload_scorings(c, {ds}));
+        RC(db_score_all(c, db, dq, m, ds, dscores));
+    }
+    const int kk = (int)std::min<int64_t>(k, nseq);
+    if (kk > 0) {
+        RC(c->result.ensure(64 * sizeof(int4)));
+        RC(db_topk(c, dscores, nseq, kk, static_cast<int2 *>(c->result.p)));
+        CU(cudaMemcpyAsync(c->stage3.p, c->result.p, (size_t)kk * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 1024, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (all_scores && nseq > 0) {
+        CU(cudaMemcpyAsync(all_scores, dscores, (size_t)nseq * sizeof(int32_t),
+                           is_device_ptr(all_scores) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    int e;
+    std::memcpy(&e, static_cast<char *>(c->stage3.p) + 1024, sizeof(int));
+    RC(map_kernel_error(e));
+    const int2 *h = static_cast<const int2 *>(c->stage3.p);
+    for (int i = 0; i < kk; ++i) hits[i] = sw_dbhit{(int64_t)h[i].x, h[i].y, 0};
+    *nhits = kk;
+    return SW_OK;
+}
