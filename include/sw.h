@@ -180,6 +180,38 @@ int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8
                      const sw_scoring *sc, sw_hit *out);
 
 /*
+ * Batched pairwise scores (many pairs of uneven lengths in one launch; the
+ * paper's Section 3.1 replaces SW#'s static block sizes by sizes derived from
+ * the sequence lengths, which this batch planner does per pair).  Pair p is
+ * a = a_res[a_off[p] .. a_off[p+1]) against b = b_res[b_off[p] .. b_off[p+1])
+ * scored with scorings[scoring_of_pair[p]]; a_off / b_off are host arrays of
+ * npairs + 1 entries starting at 0; residues may be host or device memory
+ * (device residues are used in place and must outlive the plan).  Results
+ * are the same as sw_score on each pair.
+ *
+ * A plan keeps the inputs and the task table on the device:
+ *   SW_BATCH_GRAPH     capture each run in a CUDA graph once and replay it;
+ *   SW_BATCH_AUTOTUNE  time the candidate tile shapes on this plan and keep
+ *                      the fastest (cached in the context per size class).
+ * sw_batch_run writes npairs hits (host memory).  A plan belongs to its
+ * context and must be destroyed before it.
+ */
+typedef struct sw_batch sw_batch;
+#define SW_BATCH_GRAPH     1
+#define SW_BATCH_AUTOTUNE  2
+int sw_batch_create(sw_ctx *ctx, int64_t npairs, const uint8_t *a_res, const int64_t *a_off,
+                    const uint8_t *b_res, const int64_t *b_off, const int32_t *scoring_of_pair,
+                    int32_t nscorings, const sw_scoring *scorings, int32_t flags, sw_batch **out);
+int sw_batch_run(sw_batch *plan, sw_hit *out);
+void sw_batch_destroy(sw_batch *plan);
+/* Tile shape the plan runs with: rows per lane and compute warps per block. */
+int sw_batch_config(const sw_batch *plan, int32_t *rows_per_lane, int32_t *warps);
+/* One-shot: create (no graph, no autotuning), run, destroy. */
+int sw_score_batch(sw_ctx *ctx, int64_t npairs, const uint8_t *a_res, const int64_t *a_off,
+                   const uint8_t *b_res, const int64_t *b_off, const int32_t *scoring_of_pair,
+                   int32_t nscorings, const sw_scoring *scorings, sw_hit *out);
+
+/*
  * Database of subject sequences for one-to-many search (paper Section 2.1,
  * database similarity search; Section 3.2 searches UniProtKB/Swiss-Prot).
  * residues holds all subjects back to back (codes, host or device memory),

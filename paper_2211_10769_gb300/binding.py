@@ -79,6 +79,13 @@ def load():
     lib.sw_db_destroy.restype = None
     lib.sw_db_size.argtypes = [vp]
     lib.sw_db_size.restype = i64
+    lib.sw_batch_create.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, ctypes.c_int32,
+                                    ctypes.POINTER(vp)]
+    lib.sw_batch_run.argtypes = [vp, vp]
+    lib.sw_batch_destroy.argtypes = [vp]
+    lib.sw_batch_destroy.restype = None
+    lib.sw_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.sw_score_batch.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
     lib.sw_dbsearch.argtypes = [vp, vp, vp, i64, ctypes.POINTER(_Scoring), ctypes.c_int32,
                                 ctypes.POINTER(_DbHit), ctypes.POINTER(ctypes.c_int32), vp]
     _lib = lib
@@ -193,6 +200,82 @@ class Context:
         finally:
             self._lib.sw_alignment_free(ctypes.byref(aln))
         return Alignment(aln.score, aln.a_begin, aln.a_end, aln.b_begin, aln.b_end, cig)
+
+
+SW_BATCH_GRAPH, SW_BATCH_AUTOTUNE = 1, 2
+
+
+def _pack_pairs(pairs):
+    """Concatenated residues and offsets of the a and b sides of (a, b, scoring) pairs."""
+    def cat(seqs):
+        seqs = [np.ascontiguousarray(np.asarray(x, dtype=np.uint8)) for x in seqs]
+        off = np.zeros(len(seqs) + 1, dtype=np.int64)
+        np.cumsum([len(x) for x in seqs], out=off[1:])
+        res = np.concatenate(seqs) if len(seqs) and off[-1] > 0 else np.zeros(1, np.uint8)
+        return res, off
+    ares, aoff = cat([p[0] for p in pairs])
+    bres, boff = cat([p[1] for p in pairs])
+    sidx = np.ascontiguousarray(np.array([p[2] for p in pairs], dtype=np.int32))
+    return ares, aoff, bres, boff, sidx
+
+
+def _scoring_array(scorings):
+    arr = (_Scoring * len(scorings))()
+    keep = []
+    for i, (mat, go, ge) in enumerate(scorings):
+        sc, k = _scoring(mat, go, ge)
+        arr[i] = sc
+        keep.append(k)
+    return arr, keep
+
+
+class Batch:
+    """A batch plan (sw_batch): pairs = [(a, b, scoring_index)], scorings = [(matrix, open, extend)].
+    a/b residues may be given as device tensors through `device_inputs` = (a_res, b_res) tensors
+    holding the concatenations."""
+
+    def __init__(self, ctx: Context, pairs, scorings, flags: int = 0, device_inputs=None):
+        self._lib = load()
+        self.ctx = ctx
+        self.npairs = len(pairs)
+        ares, aoff, bres, boff, sidx = _pack_pairs(pairs)
+        self._keep = [ares, aoff, bres, boff, sidx]
+        pa, pb = ares.ctypes.data, bres.ctypes.data
+        if device_inputs is not None:
+            pa, pb = device_inputs[0].data_ptr(), device_inputs[1].data_ptr()
+            self._keep.append(device_inputs)
+        arr, keep = _scoring_array(scorings)
+        self._keep += [arr, keep]
+        h = ctypes.c_void_p()
+        _check(self._lib.sw_batch_create(ctx.handle, self.npairs, pa, aoff.ctypes.data, pb, boff.ctypes.data,
+                                         sidx.ctypes.data, len(scorings), arr, int(flags), ctypes.byref(h)),
+               "sw_batch_create")
+        self.handle = h
+        self._out = (_Hit * max(1, self.npairs))()
+
+    @staticmethod
+    def packed(pairs):
+        return _pack_pairs(pairs)
+
+    def config(self):
+        r, w = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.sw_batch_config(self.handle, ctypes.byref(r), ctypes.byref(w)), "sw_batch_config")
+        return r.value, w.value
+
+    def run(self):
+        _check(self._lib.sw_batch_run(self.handle, self._out), "sw_batch_run")
+        return [Hit(h.score, h.a_end, h.b_end) for h in self._out[:self.npairs]]
+
+    def close(self):
+        if self.handle:
+            self._lib.sw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 class Database:

@@ -6,6 +6,7 @@
 #include "wavefront.cuh"
 
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 namespace swgb {
@@ -55,6 +56,7 @@ struct sw_ctx {
     swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, tb,
         tbbnd, runs, walk, misc, dbscratch, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
+    std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class
 };
 
 namespace swgb {

@@ -54,7 +54,8 @@ struct FillTask {
     const int2 *top;       // (H, F) per column of the row above, or null (matrix border)
     const int2 *left;      // (H, E) per row of the column to the left, or null (matrix border)
     const int2 *corner;    // H of the cell above-left in .x, or null (0)
-    int2 *bnd;             // bottom rows of the strips: slot (strip % nslot) * ncols
+    int2 *bnd;             // bottom rows of the strips: slot (strip % nslot) * ncols (not
+                           // written by the last strip; may be null for one-strip tasks)
     int32_t nslot;
     int32_t ckpt_every;    // also copy every ckpt_every-th strip's bottom row to ckpt (0 = never);
                            // only strips whose bottom row is inside the task: rows / (HC * ckpt_every) rows
@@ -284,6 +285,8 @@ wavefront_kernel(const FillLaunch L)
         const int strip = (int)(tk - T.ticket0);
         const int rbase = strip * HC;                   // first row of the strip within the task
         const int n = T.ncols;
+        // warps holding at least one row of the task; the others sit the strip out
+        const int Wa = min(W, (T.rows - rbase + 32 * R - 1) / (32 * R));
 
         // ---- query profile of the strip's rows: S(a_r, c) (+ open when folded)
         for (int lr = threadIdx.x; lr < HC; lr += blockDim.x) {
@@ -301,12 +304,14 @@ wavefront_kernel(const FillLaunch L)
             int in_next = 0, out_next = 0;
             long long idle = 0;
             const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
-            int2 *dst = T.bnd + (size_t)(strip % T.nslot) * n;
             // a checkpoint row only where the strip's bottom row lies inside the task
             // (the last strip may be partial)
             const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
                             (long long)(strip + 1) * HC <= (long long)T.rows;
             int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
+            // the last strip's bottom row feeds no other strip
+            const bool store = strip + 1 < T.nstrips;
+            int2 *dst = store ? T.bnd + (size_t)(strip % T.nslot) * n : nullptr;
             const int *pprev = L.prog + (tk - 1);
             int avail_prev = strip == 0 ? n : 0;
             while (out_next < n) {
@@ -315,7 +320,7 @@ wavefront_kernel(const FillLaunch L)
                     // room in channel 0 (consumer: warp 0) and in the residue ring
                     // (slowest reader: warp W-1, whose lane 31 is at column prod[W])
                     const int room0 = lds_acquire(&cons[0]) + QS;
-                    const int roomb = lds_acquire(&prod[W]) + QB - 64;
+                    const int roomb = lds_acquire(&prod[Wa]) + QB - 64;
                     int target = min(n, min(in_next + IOB, min(room0, roomb)));
                     if (target > in_next && strip > 0 && avail_prev < target) {
                         int v = 0;
@@ -335,19 +340,21 @@ wavefront_kernel(const FillLaunch L)
                         moved = true;
                     }
                 }
-                const int avail_out = lds_acquire(&prod[W]);
+                const int avail_out = lds_acquire(&prod[Wa]);
                 if (avail_out > out_next) {
-                    for (int col = out_next + lane; col < avail_out; col += 32) {
-                        const int2 u = ring[W][col & (QS - 1)];
-                        const int2 v = make_int2(u.x + go, u.y);
-                        dst[col] = v;
-                        if (ck) cdst[col] = v;
+                    if (store || ck) {
+                        for (int col = out_next + lane; col < avail_out; col += 32) {
+                            const int2 u = ring[Wa][col & (QS - 1)];
+                            const int2 v = make_int2(u.x + go, u.y);
+                            if (store) dst[col] = v;
+                            if (ck) cdst[col] = v;
+                        }
+                        __threadfence();
                     }
-                    __threadfence();
                     __syncwarp();
                     if (lane == 0) {
-                        st_release(L.prog + tk, avail_out);
-                        sts_release(&cons[W], avail_out);
+                        if (store) st_release(L.prog + tk, avail_out);
+                        sts_release(&cons[Wa], avail_out);
                     }
                     out_next = avail_out;
                     moved = true;
@@ -364,6 +371,9 @@ wavefront_kernel(const FillLaunch L)
                     __nanosleep(64);
                 }
             }
+        } else if (warp >= Wa) {
+            if constexpr (MODE != kModeTb)
+                if (lane == 0) s_cand[warp] = make_int4(0, 0x7fffffff, 0x7fffffff, 0);
         } else {
             // ================= compute warp =================
             const int lrow = (warp * 32 + lane) * R;        // first row of this lane within the strip
