@@ -241,6 +241,35 @@ int sw_dbsearch(sw_ctx *ctx, const sw_db *db, const uint8_t *q, int64_t m, const
                 int32_t k, sw_dbhit *hits, int32_t *nhits, int32_t *all_scores);
 
 /*
+ * Serving loop over a device-resident database: continuous batching of
+ * searches (same results as sw_dbsearch for every request).
+ *
+ * The database is swept circularly in `chunks` pieces; every sw_server_step
+ * runs the current piece for all admitted requests in one launch, so
+ * requests that arrive while others are on the GPU share the device with
+ * them.  A request is admitted by sw_server_submit when one of max_slots
+ * slots (1..256) is free and its device memory (about 8 bytes per database
+ * subject plus its query) fits mem_budget bytes, else SW_EAGAIN; it joins
+ * the sweep at the next step and its hits are ready after `chunks` steps
+ * (sw_server_poll: SW_EAGAIN while pending; a collected ticket is
+ * forgotten).  The scoring must allow the packed 16-bit search (every
+ * S + gap_open within int8, penalties <= 16000), else SW_ERANGE at
+ * creation; queries longer than 8000 give SW_ERANGE.  k <= 64.  The server
+ * uses its context's stream and must be destroyed before the context and
+ * the database.
+ */
+typedef struct sw_server sw_server;
+int sw_server_create(sw_ctx *ctx, const sw_db *db, const sw_scoring *sc, size_t mem_budget, int32_t k,
+                     int32_t max_slots, int32_t chunks, sw_server **out);
+int sw_server_submit(sw_server *srv, const uint8_t *q, int64_t m, uint64_t *ticket);
+/* Run one sweep step (synchronous); *active = requests that took part. */
+int sw_server_step(sw_server *srv, int32_t *active);
+int sw_server_poll(sw_server *srv, uint64_t ticket, sw_dbhit *hits, int32_t *nhits);
+/* Requests in flight, device bytes they hold, cells of retired requests. */
+int sw_server_stats(const sw_server *srv, int32_t *active, size_t *mem_used, int64_t *cells_done);
+void sw_server_destroy(sw_server *srv);
+
+/*
  * Number of kernels this context has launched since it was created
  * (diagnostics: lets a caller count device launches per call).  Returns -1
  * for a null context.

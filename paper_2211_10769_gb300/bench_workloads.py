@@ -1,0 +1,194 @@
+"""Measurements of the non-headline workloads for bench.py.
+
+Each function times one workload through the public API on cuda:0 with
+CUDA events on the context's stream and returns a small dict:
+
+* dna2k    -- sw_align of the 2,000 x 2,000 DNA pair;
+* dbsearch -- sw_dbsearch of the five protein queries (144 .. 5,478) against
+              the 500,000-subject database (top-20), plus its kernel's
+              share of the integer peak;
+* batch    -- sw_batch (one graph-captured, autotuned launch) over the 10,000
+              uneven pairs versus one sw_score call per pair;
+* serve    -- the continuous-batching server under Poisson arrivals at each
+              rate: p50 / p99 latency (arrival to result on the host),
+              sustained GCUPS, admitted / deferred submissions.
+"""
+from __future__ import annotations
+
+import statistics
+import time
+
+import numpy as np
+
+from . import workloads as W
+
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+OPS_PER_CELL = 10
+
+
+_DB_CACHE = {}
+
+
+def _protein_db():
+    """The 500,000-subject database with the five planted queries (generated once)."""
+    if "db" not in _DB_CACHE:
+        qs = W.protein_queries()
+        _DB_CACHE["db"] = (qs, W.protein_db(500_000, queries=qs))
+    return _DB_CACHE["db"]
+
+
+def _timed(torch, stream, fn, reps):
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1) / 1e3)
+    return out
+
+
+def dna2k(ctx, torch, stream, args):
+    sc = W.dna_scoring()
+    a, b = W.dna_pair_2k()
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    ctx.align(da, db, sc.matrix, sc.gap_open, sc.gap_extend)
+    ts = _timed(torch, stream, lambda: ctx.align(da, db, sc.matrix, sc.gap_open, sc.gap_extend), 20)
+    t = statistics.median(ts)
+    return {"workload": "dna_pair_2kbp_align", "cells": len(a) * len(b), "ms_median": round(1e3 * t, 3),
+            "gcups": round(len(a) * len(b) / t / 1e9, 2)}
+
+
+def dbsearch(ctx, torch, stream, args):
+    from .binding import Database
+    sc = W.protein_scoring()
+    qs, pdb = _protein_db()
+    db = Database(ctx, pdb.residues, pdb.offsets)
+    total_res = int(pdb.residues.size)
+    per_query = []
+    for q in qs:
+        db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20)
+        ts = _timed(torch, stream, lambda: db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20), 3)
+        t = statistics.median(ts)
+        per_query.append({"m": len(q), "ms": round(1e3 * t, 2), "gcups": round(len(q) * total_res / t / 1e9, 1)})
+    cells = sum(len(q) for q in qs) * total_res
+    t_all = sum(x["ms"] for x in per_query) / 1e3
+    peak16 = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6       # two 16-bit lanes per 32-bit lane
+    db.close()
+    return {"workload": "protein_dbsearch_5q_x_500k", "nseq": pdb.nseq, "residues": total_res,
+            "cells": cells, "seconds": round(t_all, 3), "gcups": round(cells / t_all / 1e9, 1),
+            "per_query": per_query,
+            "alu_frac_16bit_lanes": round(OPS_PER_CELL * cells / t_all / peak16, 4)}
+
+
+def batch(ctx, torch, stream, args):
+    from . import binding
+    d, p = W.dna_scoring(), W.protein_scoring()
+    scorings = [(d.matrix, d.gap_open, d.gap_extend), (p.matrix, p.gap_open, p.gap_extend)]
+    raw = W.batch_pairs(10_000)
+    pairs = [(a, b, 0 if kind == "dna" else 1) for a, b, kind in raw]
+    cells = sum(len(a) * len(b) for a, b, _ in pairs)
+    ares, aoff, bres, boff, sidx = binding.Batch.packed(pairs)
+    dev = (torch.from_numpy(ares).cuda(), torch.from_numpy(bres).cuda())
+    plan = binding.Batch(ctx, pairs, scorings, flags=binding.SW_BATCH_GRAPH | binding.SW_BATCH_AUTOTUNE,
+                         device_inputs=dev)
+    plan.run()
+    ts = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        plan.run()
+        ts.append(time.perf_counter() - t0)
+    t_batch = statistics.median(ts)
+    cfg = plan.config()
+    plan.close()
+    # one sw_score launch per pair, inputs already on the device
+    dpairs = []
+    for k, (a, b, si) in enumerate(pairs):
+        dpairs.append((dev[0][int(aoff[k]):int(aoff[k + 1])], dev[1][int(boff[k]):int(boff[k + 1])], si))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b, si in dpairs:
+        mat, go, ge = scorings[si]
+        ctx.score(a, b, mat, go, ge)
+    t_pair = time.perf_counter() - t0
+    return {"workload": "batch_10k_uneven_pairs", "cells": cells, "batched_s": round(t_batch, 4),
+            "batched_gcups": round(cells / t_batch / 1e9, 1), "per_pair_s": round(t_pair, 3),
+            "per_pair_gcups": round(cells / t_pair / 1e9, 1), "speedup": round(t_pair / t_batch, 2),
+            "tile": {"rows_per_lane": cfg[0], "warps": cfg[1]}, "timing": "wall clock incl. host copy of results"}
+
+
+def serve(ctx, torch, stream, args):
+    from . import binding
+    sc = W.protein_scoring()
+    qs, pdb = _protein_db()
+    db = binding.Database(ctx, pdb.residues, pdb.offsets)
+    total_res = int(pdb.residues.size)
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    out = []
+    for rate in rates:
+        reqs = W.serving_requests(args.serve_requests, rate)
+        srv = binding.Server(ctx, db, sc.matrix, sc.gap_open, sc.gap_extend, mem_budget=8 << 30, k=20,
+                             max_slots=64, chunks=8)
+        queue, inflight, lat = [], {}, []
+        deferred = 0
+        nxt, ndone, steps = 0, 0, 0
+        t0 = time.perf_counter()
+        busy = 0.0
+        while ndone < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt][0] <= now:
+                queue.append(nxt)
+                nxt += 1
+            while queue:
+                t = srv.submit(reqs[queue[0]][1])
+                if t is None:
+                    deferred += 1
+                    break
+                inflight[t] = queue.pop(0)
+            if inflight:
+                s0 = time.perf_counter()
+                srv.step()
+                busy += time.perf_counter() - s0
+                steps += 1
+                done_now = time.perf_counter() - t0
+                for t, i in list(inflight.items()):
+                    r = srv.poll(t)
+                    if r is not None:
+                        lat.append(done_now - reqs[i][0])
+                        del inflight[t]
+                        ndone += 1
+            elif nxt < len(reqs):
+                time.sleep(max(0.0, min(0.01, reqs[nxt][0] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        cells = sum(len(q) for _, q in reqs) * total_res
+        srv.close()
+        lat.sort()
+        out.append({"rate_per_s": rate, "requests": len(reqs), "p50_s": round(float(np.percentile(lat, 50)), 3),
+                    "p99_s": round(float(np.percentile(lat, 99)), 3), "sustained_gcups": round(cells / wall / 1e9, 1),
+                    "busy_gcups": round(cells / busy / 1e9, 1), "steps": steps, "deferred_submits": deferred,
+                    "offered_gcups": round(rate * cells / len(reqs) / 1e9, 1)})
+    db.close()
+    return {"workload": "serving_poisson_protein_vs_500k", "chunks": 8, "max_slots": 64, "k": 20,
+            "note": "offered load exceeds device capacity at every rate; latency is queue-dominated",
+            "rates": out}
+
+
+def run_all(names, args):
+    import torch
+    from .binding import Context
+    stream = torch.cuda.current_stream()
+    ctx = Context(0, stream)
+    res = {}
+    for nm in names:
+        fn = {"dna2k": dna2k, "dbsearch": dbsearch, "batch": batch, "serve": serve}[nm]
+        t0 = time.perf_counter()
+        try:
+            res[nm] = fn(ctx, torch, stream, args)
+        except Exception as exc:  # noqa: BLE001 - report, keep the headline line
+            res[nm] = {"error": repr(exc)}
+        res[nm]["bench_wall_s"] = round(time.perf_counter() - t0, 1)
+    ctx.close()
+    return res

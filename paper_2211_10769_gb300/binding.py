@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -86,6 +87,15 @@ def load():
     lib.sw_batch_destroy.restype = None
     lib.sw_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.sw_score_batch.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
+    lib.sw_server_create.argtypes = [vp, vp, ctypes.POINTER(_Scoring), ctypes.c_size_t, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
+    lib.sw_server_submit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.sw_server_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.sw_server_poll.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.sw_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.sw_server_destroy.argtypes = [vp]
+    lib.sw_server_destroy.restype = None
     lib.sw_dbsearch.argtypes = [vp, vp, vp, i64, ctypes.POINTER(_Scoring), ctypes.c_int32,
                                 ctypes.POINTER(_DbHit), ctypes.POINTER(ctypes.c_int32), vp]
     _lib = lib
@@ -148,9 +158,16 @@ class Context:
         _check(self._lib.sw_ctx_create(int(device), handle, ctypes.byref(h)), "sw_ctx_create")
         self.handle = h
         self.device = device
+        self._children = weakref.WeakSet()
+
+    def _adopt(self, obj):
+        """Objects built on this context are closed before it."""
+        self._children.add(obj)
 
     def close(self):
         if self.handle:
+            for ch in list(self._children):
+                ch.close()
             self._lib.sw_ctx_destroy(self.handle)
             self.handle = None
 
@@ -252,6 +269,7 @@ class Batch:
                "sw_batch_create")
         self.handle = h
         self._out = (_Hit * max(1, self.npairs))()
+        ctx._adopt(self)
 
     @staticmethod
     def packed(pairs):
@@ -291,9 +309,16 @@ class Database:
                                       off.ctypes.data, len(off) - 1, ctypes.byref(h)), "sw_db_create")
         self.handle = h
         self.nseq = len(off) - 1
+        self._children = weakref.WeakSet()
+        ctx._adopt(self)
+
+    def _adopt(self, obj):
+        self._children.add(obj)
 
     def close(self):
         if self.handle:
+            for ch in list(self._children):
+                ch.close()
             self._lib.sw_db_destroy(self.handle)
             self.handle = None
 
@@ -320,6 +345,64 @@ class Database:
         _check(self._lib.sw_dbsearch(self.ctx.handle, self.handle, pq, m, ctypes.byref(sc), int(k),
                                      hits, ctypes.byref(nh), ptr), "sw_dbsearch")
         return [(int(hits[i].subject), int(hits[i].score)) for i in range(nh.value)], out
+
+
+class Server:
+    """Continuous-batching search server over a Database (sw_server)."""
+
+    def __init__(self, ctx: Context, db: Database, matrix, gap_open: int, gap_extend: int,
+                 mem_budget: int, k: int = 20, max_slots: int = 32, chunks: int = 16):
+        self._lib = load()
+        self.ctx, self.db, self.k = ctx, db, k
+        self._sc, self._keep = _scoring(matrix, gap_open, gap_extend)
+        h = ctypes.c_void_p()
+        _check(self._lib.sw_server_create(ctx.handle, db.handle, ctypes.byref(self._sc), int(mem_budget), int(k),
+                                          int(max_slots), int(chunks), ctypes.byref(h)), "sw_server_create")
+        self.handle = h
+        self._hits = (_DbHit * max(1, k))()
+        ctx._adopt(self)
+        db._adopt(self)
+
+    def submit(self, q):
+        """Ticket of the admitted request, or None when no slot / memory is free."""
+        pq, m, keep = _seq(q)
+        t = ctypes.c_uint64()
+        rc = self._lib.sw_server_submit(self.handle, pq, m, ctypes.byref(t))
+        if rc == SW_EAGAIN:
+            return None
+        _check(rc, "sw_server_submit")
+        return int(t.value)
+
+    def step(self) -> int:
+        a = ctypes.c_int32()
+        _check(self._lib.sw_server_step(self.handle, ctypes.byref(a)), "sw_server_step")
+        return a.value
+
+    def poll(self, ticket: int):
+        """[(subject, score)] when finished, None while pending."""
+        n = ctypes.c_int32()
+        rc = self._lib.sw_server_poll(self.handle, ctypes.c_uint64(ticket), self._hits, ctypes.byref(n))
+        if rc == SW_EAGAIN:
+            return None
+        _check(rc, "sw_server_poll")
+        return [(int(self._hits[i].subject), int(self._hits[i].score)) for i in range(n.value)]
+
+    def stats(self):
+        a, mu, cells = ctypes.c_int32(), ctypes.c_size_t(), ctypes.c_int64()
+        _check(self._lib.sw_server_stats(self.handle, ctypes.byref(a), ctypes.byref(mu), ctypes.byref(cells)),
+               "sw_server_stats")
+        return a.value, mu.value, cells.value
+
+    def close(self):
+        if self.handle:
+            self._lib.sw_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 PROBE_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,

@@ -33,7 +33,9 @@ struct DbJob {
     const uint8_t *q;          // query codes (device)
     int32_t m;                 // query length
     int32_t scoring;           // index into the scoring table
-    int32_t pair0, pair1;      // pairs [pair0, pair1) of the sorted database
+    int32_t pair0, pair1;      // pairs pair0, pair0 + stride, ... below pair1 of the sorted database
+    int32_t pair_stride;
+    int32_t block0;            // first block of the launch working on this job (prefix over jobs)
     int32_t *scores;           // per subject (original index): score, or -1 when flagged
     int32_t *ovf;              // flagged subject ids
     int32_t *novf;             // their count
@@ -86,15 +88,22 @@ __device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R
     }
 }
 
-// grid: (blocks, jobs); block: W warps.  Dynamic shared memory: the query
-// profile, (K + 1) * mpad bytes, mpad = passes * 32 * R.
+// grid: 1D; blocks [jobs[j].block0, jobs[j+1].block0) work on job j (the
+// host gives each job blocks in proportion to its work); block: W warps.
+// Dynamic shared memory: the query profile, (K + 1) * mpad bytes,
+// mpad = passes * 32 * R.
 template <int R, int W>
 __global__ void __launch_bounds__(W * 32)
-db_s16x2_kernel(const DbJob *__restrict__ jobs, const DbView D, const DevScoring *__restrict__ scorings,
-                uint2 *__restrict__ scratch)
+db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
+                const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {
     extern __shared__ __align__(16) int8_t prof[];
-    const DbJob &J = jobs[blockIdx.y];
+    int jlo = 0, jhi = njobs - 1;                 // last job with block0 <= blockIdx.x
+    while (jlo < jhi) {
+        const int mid = (jlo + jhi + 1) >> 1;
+        if (jobs[mid].block0 <= (int)blockIdx.x) jlo = mid; else jhi = mid - 1;
+    }
+    const DbJob &J = jobs[jlo];
     const DevScoring &SC = scorings[J.scoring];
     const int K = SC.K, go = SC.go, ge = SC.ge;
     const int m = J.m;
@@ -113,14 +122,14 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, const DbView D, const DevScoring
     for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
     const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
     const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.y * gridDim.x + blockIdx.x) * W + (threadIdx.x >> 5);
+    const int gwarp = blockIdx.x * W + (threadIdx.x >> 5);
     uint2 *bnd = scratch + (size_t)gwarp * (size_t)D.maxlen;
     const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
     const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
 
     for (;;) {
         int p = 0;
-        if (lane == 0) p = atomicAdd(J.next_pair, 1) + J.pair0;
+        if (lane == 0) p = J.pair0 + atomicAdd(J.next_pair, 1) * J.pair_stride;
         p = __shfl_sync(kFull, p, 0);
         if (p >= J.pair1) break;
         const int sa = D.pairs[2 * p], sb = D.pairs[2 * p + 1];
@@ -227,7 +236,7 @@ __device__ __forceinline__ unsigned long long topk_key(int score, int s) {
 constexpr int kTopkThreads = 256;
 constexpr int kTopkChunk = 2048;
 
-__device__ void block_topk(unsigned long long *keys, int count, int k, unsigned long long *out) {
+static __device__ void block_topk(unsigned long long *keys, int count, int k, unsigned long long *out) {
     __shared__ unsigned long long red[kTopkThreads / 32];
     __shared__ int redi[kTopkThreads / 32];
     for (int it = 0; it < k; ++it) {

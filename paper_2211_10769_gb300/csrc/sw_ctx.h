@@ -77,8 +77,19 @@ int reset_err(sw_ctx *c);
 int validate_codes(sw_ctx *c, const uint8_t *d, int64_t len, int K);
 int read_err(sw_ctx *c, int *e);
 // database search pieces shared with the serving loop
+struct DbJob;
+struct DbView;
 int db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
                  int32_t *dscores);
+int db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
+               const std::vector<int32_t> &flagged, int32_t *dscores);
 int db_topk(sw_ctx *c, const int32_t *dscores, int64_t nseq, int k, int2 *dout);
+int db_shape(int K, int m);
+int db_resident_blocks(sw_ctx *c, int K, int m, int *out);
+int db_warps_per_block(int K, int m);
+int db_launch(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m);
+int db_view(const sw_db *db, DbView *v, int64_t *nseq, int32_t *max_code, int *device);
+int db_chunk_maxlen(const sw_db *db, int32_t pair0, int32_t pair1);
+int64_t db_total_residues(const sw_db *db);
 
 }  // namespace swgb

@@ -24,6 +24,7 @@ struct sw_db {
     int32_t maxlen = 0;
     int32_t max_code = -1;
     std::vector<int64_t> off;           // host copy of the offsets
+    std::vector<int32_t> hpairs;        // host copy of the length-sorted pairs
     DevBuf res, doff, pairs;
 };
 
@@ -41,42 +42,93 @@ static __global__ void max_code_kernel(const uint8_t *s, long long len, int *out
 constexpr long long kMaxProfileSmem = 200 * 1024;
 
 template <int R, int W>
-int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, const DbView &D, int K, int m, int *grid_out) {
+int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m) {
     auto kern = db_s16x2_kernel<R, W>;
+    constexpr int ROWS = 32 * R;
+    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
+    const size_t smem = (size_t)(K + 1) * (size_t)mpad;
+    // boundary rows: one per warp
+    RC(c->dbscratch.ensure((size_t)nblocks * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
+                                                         static_cast<const DevScoring *>(c->scorings.p),
+                                                         static_cast<uint2 *>(c->dbscratch.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    return SW_OK;
+}
+
+template <int R, int W>
+int resident_blocks(sw_ctx *c, int K, int m, int *out) {
     constexpr int ROWS = 32 * R;
     const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
     const size_t smem = (size_t)(K + 1) * (size_t)mpad;
     if ((long long)smem > kMaxProfileSmem) return SW_ERANGE;
     static int attr_set[64] = {0};
     if (c->device < 64 && !attr_set[c->device]) {
-        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxProfileSmem));
+        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxProfileSmem));
         attr_set[c->device] = 1;
     }
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, W * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W>, W * 32, smem));
     if (occ < 1) return SW_ECUDA;
-    const int gx = std::max(1, std::min(occ * c->nsm, (D.npairs + W - 1) / W));
-    // boundary rows: one per warp
-    RC(c->dbscratch.ensure((size_t)gx * njobs * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
-    dim3 grid((unsigned)gx, (unsigned)njobs);
-    kern<<<grid, W * 32, smem, c->stream>>>(jobs, D, static_cast<const DevScoring *>(c->scorings.p),
-                                           static_cast<uint2 *>(c->dbscratch.p));
-    CU(cudaGetLastError());
-    ++c->launches;
-    if (grid_out) *grid_out = gx;
+    *out = occ * c->nsm;
     return SW_OK;
 }
 
 // Tile shape by query length: the whole profile must sit in shared memory;
 // long queries use one block of 32 warps per SM.
-int launch_db_auto(sw_ctx *c, const DbJob *jobs, int njobs, const DbView &D, int K, int m) {
+}  // namespace
+
+// Tile shape by the longest query of the launch: the whole profile must sit
+// in shared memory; long queries use one block of 32 warps per SM.
+int swgb::db_shape(int K, int m) {
     const long long prof8 = (long long)(K + 1) * (((m + 255) / 256) * 256);
-    if (prof8 > 96 * 1024) return launch_db<8, 32>(c, jobs, njobs, D, K, m, nullptr);
-    if (m >= 1024) return launch_db<16, 8>(c, jobs, njobs, D, K, m, nullptr);
-    return launch_db<8, 8>(c, jobs, njobs, D, K, m, nullptr);
+    if (prof8 > 96 * 1024) return 2;
+    return m >= 1024 ? 1 : 0;
 }
 
-}  // namespace
+int swgb::db_resident_blocks(sw_ctx *c, int K, int m, int *out) {
+    switch (db_shape(K, m)) {
+        case 2: return resident_blocks<8, 32>(c, K, m, out);
+        case 1: return resident_blocks<16, 8>(c, K, m, out);
+        default: return resident_blocks<8, 8>(c, K, m, out);
+    }
+}
+
+int swgb::db_warps_per_block(int K, int m) { return db_shape(K, m) == 2 ? 32 : 8; }
+
+int swgb::db_launch(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m) {
+    switch (db_shape(K, m)) {
+        case 2: return launch_db<8, 32>(c, jobs, njobs, nblocks, D, K, m);
+        case 1: return launch_db<16, 8>(c, jobs, njobs, nblocks, D, K, m);
+        default: return launch_db<8, 8>(c, jobs, njobs, nblocks, D, K, m);
+    }
+}
+
+int swgb::db_view(const sw_db *db, DbView *v, int64_t *nseq, int32_t *max_code, int *device) {
+    v->res = static_cast<const uint8_t *>(db->res.p);
+    v->off = static_cast<const int64_t *>(db->doff.p);
+    v->pairs = static_cast<const int32_t *>(db->pairs.p);
+    v->npairs = db->npairs;
+    v->maxlen = db->maxlen;
+    *nseq = db->nseq;
+    *max_code = db->max_code;
+    *device = db->device;
+    return SW_OK;
+}
+
+int64_t swgb::db_total_residues(const sw_db *db) { return db->off.empty() ? 0 : db->off.back(); }
+
+int swgb::db_chunk_maxlen(const sw_db *db, int32_t pair0, int32_t pair1) {
+    int64_t mx = 0;
+    for (int32_t p = pair0; p < pair1 && p < db->npairs; ++p)
+        for (int h = 0; h < 2; ++h) {
+            const int32_t s = db->hpairs[(size_t)(2 * p + h)];
+            if (s >= 0) mx = std::max(mx, db->off[(size_t)s + 1] - db->off[(size_t)s]);
+        }
+    return (int)mx;
+}
 
 extern "C" int sw_db_create(sw_ctx *c, const uint8_t *residues, const int64_t *offsets, int64_t nseq,
                             sw_db **out) {
@@ -109,6 +161,7 @@ extern "C" int sw_db_create(sw_ctx *c, const uint8_t *residues, const int64_t *o
     int64_t maxlen = 0;
     for (int64_t s = 0; s < nseq; ++s) maxlen = std::max(maxlen, offsets[s + 1] - offsets[s]);
     db->maxlen = (int32_t)maxlen;
+    db->hpairs = pairs;
     rc = db->pairs.ensure(std::max<size_t>(1, pairs.size()) * sizeof(int32_t));
     if (rc) { delete db; return rc; }
     const cudaMemcpyKind kind = is_device_ptr(residues) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -155,7 +208,7 @@ int swgb::db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m,
     CU(cudaMemsetAsync(novf, 0, 2 * sizeof(int32_t), c->stream));
     DbJob job;
     job.q = dq; job.m = (int32_t)m; job.scoring = 0;
-    job.pair0 = 0; job.pair1 = db->npairs;
+    job.pair0 = 0; job.pair1 = db->npairs; job.pair_stride = 1; job.block0 = 0;
     job.scores = dscores;
     job.ovf = static_cast<int32_t *>(c->dbovf.p);
     job.novf = novf; job.next_pair = next;
@@ -171,7 +224,16 @@ int swgb::db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m,
     int32_t nflag = 0;
     std::vector<int32_t> flagged;
     const bool packed_ok = fold_open(ds) && ds.go <= 16000 && ds.ge <= 16000;
-    int rc = packed_ok ? launch_db_auto(c, static_cast<const DbJob *>(c->dbjob.p), 1, D, K, (int)m) : SW_ERANGE;
+    int rc = SW_ERANGE;
+    if (packed_ok) {
+        int nblk = 0;
+        rc = db_resident_blocks(c, K, (int)m, &nblk);
+        if (!rc) {
+            const int W = db_warps_per_block(K, (int)m);
+            nblk = std::max(1, std::min(nblk, (db->npairs + W - 1) / W));
+            rc = db_launch(c, static_cast<const DbJob *>(c->dbjob.p), 1, nblk, D, K, (int)m);
+        }
+    }
     if (rc == SW_ERANGE) {
         // the packed kernel cannot take this query / scoring: score every subject in int32
         flagged.resize((size_t)db->nseq);
@@ -187,7 +249,15 @@ int swgb::db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m,
         }
     }
     if (flagged.empty()) return SW_OK;
-    // exact rescoring: one int32 wavefront task per flagged subject (query down the rows)
+    return db_rescore(c, db, dq, m, ds, flagged, dscores);
+}
+
+// Exact rescoring: one int32 wavefront task per flagged subject (query down
+// the rows); scores[flagged[k]] receives the result.
+int swgb::db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
+                     const std::vector<int32_t> &flagged, int32_t *dscores) {
+    const int K = ds.K;
+    RC(upload_scorings(c, {ds}));
     const int HC = fill_rows_per_strip(c->fwd);
     std::vector<FillTask> tasks;
     tasks.reserve(flagged.size());

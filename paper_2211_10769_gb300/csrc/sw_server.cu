@@ -1,0 +1,254 @@
+// sw_server.cu -- serving loop: continuous batching of database searches
+// against a device-resident database.
+//
+// The database (sorted by length) is cut into C chunks of subject pairs.
+// Active requests sweep it circularly: one server step launches the packed
+// 16-bit search over the current chunk for every active request at once
+// (one job per request; blocks of all jobs run concurrently and share the
+// chunk's residues through L2).  A request is admitted into a free slot as
+// soon as one exists and its device memory fits the budget, joins the sweep
+// at the next step, and retires after it has visited all C chunks: its
+// flagged subjects are rescored exactly in 32 bits and its top-k hits are
+// taken from its per-request score array, which lives on the device for the
+// request's whole life.  A request's result does not depend on which other
+// requests shared its steps.
+#include "sw.h"
+#include "sw_ctx.h"
+#include "dbsearch.cuh"
+#include "wavefront.cuh"
+#include "aux_kernels.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <vector>
+
+using namespace swgb;
+
+#define CU(x) do { if ((x) != cudaSuccess) { cudaGetLastError(); return SW_ECUDA; } } while (0)
+#define RC(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+
+namespace {
+
+struct Slot {
+    bool active = false;
+    uint64_t ticket = 0;
+    int64_t m = 0;
+    int visited = 0;
+    DevBuf q, scores, ovf, ctr;      // ctr: [novf, next_pair]
+};
+
+struct Done {
+    int status = SW_OK;
+    std::vector<sw_dbhit> hits;
+};
+
+}  // namespace
+
+struct sw_server {
+    sw_ctx *c = nullptr;
+    const sw_db *db = nullptr;
+    DevScoring ds;
+    int k = 20;
+    size_t mem_budget = 0, mem_used = 0;
+    int chunks = 16;
+    int cur_chunk = 0;
+    uint64_t next_ticket = 1;
+    std::vector<Slot> slots;
+    std::map<uint64_t, Done> done;
+    DevBuf jobs;
+    HostBuf hjobs;
+    DbView view{};
+    int64_t nseq = 0;
+    int maxK = 0;
+    long long cells_done = 0;       // cells of retired requests
+    int64_t total_res = 0;
+};
+
+namespace {
+
+size_t slot_bytes(const sw_server *S, int64_t m) {
+    return (size_t)m + 256 + 2 * (size_t)std::max<int64_t>(1, S->nseq) * sizeof(int32_t) + 256;
+}
+
+// Retire a request that has seen every chunk: exact rescoring, top-k, free.
+int retire(sw_server *S, Slot &s) {
+    sw_ctx *c = S->c;
+    Done d;
+    int32_t nflag = 0;
+    CU(cudaMemcpyAsync(c->stage3.p, s.ctr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    std::memcpy(&nflag, c->stage3.p, sizeof(int32_t));
+    if (nflag > 0) {
+        // rescore the flagged subjects exactly: reuse the search path's rescoring on this slot
+        std::vector<int32_t> flagged((size_t)nflag);
+        CU(cudaMemcpy(flagged.data(), s.ovf.p, (size_t)nflag * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        RC(db_rescore(c, S->db, static_cast<const uint8_t *>(s.q.p), s.m, S->ds, flagged,
+                      static_cast<int32_t *>(s.scores.p)));
+    }
+    const int kk = (int)std::min<int64_t>(S->k, S->nseq);
+    if (kk > 0) {
+        RC(c->result.ensure(64 * sizeof(int4)));
+        RC(db_topk(c, static_cast<const int32_t *>(s.scores.p), S->nseq, kk, static_cast<int2 *>(c->result.p)));
+        CU(cudaMemcpyAsync(c->stage3.p, c->result.p, (size_t)kk * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        const int2 *h = static_cast<const int2 *>(c->stage3.p);
+        for (int i = 0; i < kk; ++i) d.hits.push_back(sw_dbhit{(int64_t)h[i].x, h[i].y, 0});
+    }
+    S->done[s.ticket] = std::move(d);
+    S->cells_done += (long long)s.m * S->total_res;
+    S->mem_used -= slot_bytes(S, s.m);
+    s.active = false;
+    s.q.release(); s.scores.release(); s.ovf.release(); s.ctr.release();
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" int sw_server_create(sw_ctx *c, const sw_db *db, const sw_scoring *sc, size_t mem_budget, int32_t k,
+                                int32_t max_slots, int32_t chunks, sw_server **out) {
+    if (!c || !db || !out || k < 0 || k > 64 || max_slots < 1 || max_slots > 256 || chunks < 1) return SW_EINVAL;
+    DevScoring ds;
+    RC(check_scoring(sc, &ds));
+    if (!fold_open(ds) || ds.go > 16000 || ds.ge > 16000) return SW_ERANGE;   // needs the packed kernel
+    sw_server *S = new (std::nothrow) sw_server();
+    if (!S) return SW_ENOMEM;
+    S->c = c;
+    S->db = db;
+    S->ds = ds;
+    S->k = k;
+    S->mem_budget = mem_budget;
+    S->slots.resize((size_t)max_slots);
+    int32_t max_code = 0;
+    int dev = 0;
+    db_view(db, &S->view, &S->nseq, &max_code, &dev);
+    if (dev != c->device || max_code >= ds.K) { delete S; return SW_EINVAL; }
+    S->chunks = std::max(1, std::min<int>(chunks, std::max(1, S->view.npairs)));
+    S->total_res = db_total_residues(db);
+    S->maxK = ds.K;
+    *out = S;
+    return SW_OK;
+}
+
+extern "C" int sw_server_submit(sw_server *S, const uint8_t *q, int64_t m, uint64_t *ticket) {
+    if (!S || !ticket || m < 0 || (m > 0 && !q)) return SW_EINVAL;
+    if (m > 8000) return SW_ERANGE;                  // the query profile must fit shared memory
+    Slot *free_slot = nullptr;
+    for (Slot &s : S->slots) if (!s.active) { free_slot = &s; break; }
+    const size_t need = slot_bytes(S, m);
+    if (!free_slot || S->mem_used + need > S->mem_budget) return SW_EAGAIN;
+    sw_ctx *c = S->c;
+    DeviceGuard g(c->device);
+    Slot &s = *free_slot;
+    RC(s.q.ensure((size_t)m + 16));
+    RC(s.scores.ensure((size_t)std::max<int64_t>(1, S->nseq) * sizeof(int32_t)));
+    RC(s.ovf.ensure((size_t)std::max<int64_t>(1, S->nseq) * sizeof(int32_t)));
+    RC(s.ctr.ensure(64));
+    if (m > 0) CU(cudaMemcpyAsync(s.q.p, q, (size_t)m, is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(s.scores.p, 0, (size_t)std::max<int64_t>(1, S->nseq) * sizeof(int32_t), c->stream));
+    CU(cudaMemsetAsync(s.ctr.p, 0, 64, c->stream));
+    RC(reset_err(c));
+    if (m > 0) RC(validate_codes(c, static_cast<const uint8_t *>(s.q.p), m, S->ds.K));
+    int e = 0;
+    RC(read_err(c, &e));
+    if (e) return map_kernel_error(e);
+    s.active = true;
+    s.ticket = S->next_ticket++;
+    s.m = m;
+    s.visited = (m == 0 || S->nseq == 0) ? S->chunks : 0;
+    S->mem_used += need;
+    *ticket = s.ticket;
+    if (s.visited >= S->chunks) RC(retire(S, s));
+    return SW_OK;
+}
+
+// One sweep step: every active request processes the current chunk.
+extern "C" int sw_server_step(sw_server *S, int32_t *active) {
+    if (!S) return SW_EINVAL;
+    sw_ctx *c = S->c;
+    DeviceGuard g(c->device);
+    std::vector<Slot *> act;
+    for (Slot &s : S->slots) if (s.active) act.push_back(&s);
+    if (active) *active = (int32_t)act.size();
+    if (act.empty()) return SW_OK;
+    // chunk c = pairs c, c + C, c + 2C, ...: every chunk mixes long and short subjects
+    const int np = S->view.npairs;
+    const int p0 = S->cur_chunk, p1 = np, stride = S->chunks;
+    int64_t maxm = 0, summ = 0;
+    for (Slot *s : act) { maxm = std::max(maxm, s->m); summ += s->m; }
+    int resident = 0;
+    RC(db_resident_blocks(c, S->ds.K, (int)maxm, &resident));
+    const int W = db_warps_per_block(S->ds.K, (int)maxm);
+    const int chunk_pairs = p0 < np ? (np - p0 + stride - 1) / stride : 0;
+    std::vector<DbJob> jobs;
+    int nblocks = 0;
+    for (Slot *s : act) {
+        DbJob j;
+        j.q = static_cast<const uint8_t *>(s->q.p);
+        j.m = (int32_t)s->m;
+        j.scoring = 0;
+        j.pair0 = p0; j.pair1 = p1; j.pair_stride = stride;
+        // blocks in proportion to the request's share of the step's work
+        const int share = (int)((double)resident * (double)s->m / (double)std::max<int64_t>(1, summ) + 0.5);
+        const int nb = std::max(1, std::min(share, (chunk_pairs + W - 1) / W));
+        j.block0 = nblocks;
+        nblocks += nb;
+        j.scores = static_cast<int32_t *>(s->scores.p);
+        j.ovf = static_cast<int32_t *>(s->ovf.p);
+        j.novf = static_cast<int32_t *>(s->ctr.p);
+        j.next_pair = static_cast<int32_t *>(s->ctr.p) + 1;
+        jobs.push_back(j);
+    }
+    const size_t jb = jobs.size() * sizeof(DbJob);
+    RC(S->jobs.ensure(jb));
+    RC(S->hjobs.ensure(jb));
+    std::memcpy(S->hjobs.p, jobs.data(), jb);
+    RC(upload_scorings(c, {S->ds}));
+    CU(cudaMemcpyAsync(S->jobs.p, S->hjobs.p, jb, cudaMemcpyHostToDevice, c->stream));
+    for (Slot *s : act) CU(cudaMemsetAsync(static_cast<int32_t *>(s->ctr.p) + 1, 0, sizeof(int32_t), c->stream));
+    if (chunk_pairs > 0) {
+        DbView v = S->view;
+        v.maxlen = std::max(1, db_chunk_maxlen(S->db, p0, p0 + 1));     // pairs are sorted longest first
+        RC(db_launch(c, static_cast<const DbJob *>(S->jobs.p), (int)jobs.size(), nblocks, v, S->ds.K, (int)maxm));
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    S->cur_chunk = (S->cur_chunk + 1) % S->chunks;
+    for (Slot *s : act) {
+        if (++s->visited >= S->chunks) RC(retire(S, *s));
+    }
+    return SW_OK;
+}
+
+extern "C" int sw_server_poll(sw_server *S, uint64_t ticket, sw_dbhit *hits, int32_t *nhits) {
+    if (!S || !nhits) return SW_EINVAL;
+    auto it = S->done.find(ticket);
+    if (it == S->done.end()) {
+        for (const Slot &s : S->slots) if (s.active && s.ticket == ticket) return SW_EAGAIN;
+        return SW_EINVAL;                            // unknown or already collected
+    }
+    if (!it->second.hits.empty() && !hits) return SW_EINVAL;
+    const int st = it->second.status;
+    for (size_t i = 0; i < it->second.hits.size(); ++i) hits[i] = it->second.hits[i];
+    *nhits = (int32_t)it->second.hits.size();
+    S->done.erase(it);
+    return st;
+}
+
+extern "C" int sw_server_stats(const sw_server *S, int32_t *active, size_t *mem_used, int64_t *cells_done) {
+    if (!S) return SW_EINVAL;
+    int a = 0;
+    for (const Slot &s : S->slots) a += s.active ? 1 : 0;
+    if (active) *active = a;
+    if (mem_used) *mem_used = S->mem_used;
+    if (cells_done) *cells_done = S->cells_done;
+    return SW_OK;
+}
+
+extern "C" void sw_server_destroy(sw_server *S) {
+    if (!S) return;
+    DeviceGuard g(S->c->device);
+    cudaStreamSynchronize(S->c->stream);
+    delete S;
+}
