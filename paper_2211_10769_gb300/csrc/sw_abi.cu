@@ -137,10 +137,10 @@ int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
         attr_set[c->device] = 1;
     }
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (W + 1) * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (W + 2) * 32, smem));
     if (occ < 1) return SW_ECUDA;
     const long long grid = std::min<long long>(tickets, (long long)occ * c->nsm);
-    kern<<<(unsigned)grid, (W + 1) * 32, smem, c->stream>>>(L);
+    kern<<<(unsigned)grid, (W + 2) * 32, smem, c->stream>>>(L);
     CU(cudaGetLastError());
     ++c->launches;
     return SW_OK;

@@ -15,11 +15,13 @@
 //   * Warps hand their bottom row to the next warp through shared-memory
 //     rings guarded by acquire/release counters (no block barriers in the
 //     sweep); every wait is bounded.
-//   * A separate I/O warp streams the strip's top boundary row and the
-//     column residues into shared memory, ahead of warp 0, and drains the
-//     strip's bottom row to global memory, publishing how many columns are
-//     stored with st.release.gpu; the next strip's I/O warp reads that
-//     counter with ld.acquire.gpu.
+//   * Two I/O warps move data between global and shared memory: the input
+//     warp streams the strip's top boundary row and the column residues
+//     ahead of warp 0; the output warp drains the strip's bottom row to
+//     global memory and publishes how many columns are stored with
+//     st.release.gpu, which the next strip's input warp reads with
+//     ld.acquire.gpu.  Keeping them apart means polling for input never
+//     delays the output the next strip is waiting for.
 //   * Strips are claimed from a global ticket counter in order, so a strip
 //     only waits on strips already held by running blocks.
 //
@@ -117,26 +119,24 @@ __device__ __forceinline__ void sts_release(int *p, int v) {
     asm volatile("st.release.cta.shared.b32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 
-// Lane 0 waits until *ctr >= want (bounded); the result is broadcast.  false
-// on timeout or when the block is aborting.
+// The warp waits until *ctr >= want (bounded).  Every lane reads the counter
+// with acquire semantics, so the common case (already there) is one uniform
+// check; false on timeout or when the block is aborting.
 __device__ __forceinline__ bool warp_wait_geq(const int *ctr, int want, const volatile int *abort_flag,
                                               long long limit, int *err) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) {
-        long long it = 0;
-        while (lds_acquire(ctr) < want) {
-            if (*abort_flag) { ok = 0; break; }
-            if (++it > limit) { atomicCAS(err, 0, kErrTimeout); ok = 0; break; }
-            __nanosleep(20);
-        }
+    if (lds_acquire(ctr) >= want) return true;
+    long long it = 0;
+    while (lds_acquire(ctr) < want) {
+        if (*abort_flag) return false;
+        if (++it > limit) { atomicCAS(err, 0, kErrTimeout); return false; }
+        if (it > 64) __nanosleep(20);              // spin first: the producer is usually a step away
     }
-    __syncwarp();                       // orders the other lanes' reads after lane 0's acquire
-    return __shfl_sync(kFull, ok, 0) != 0;
+    return true;
 }
 
 enum FillMode { kModeScore = 0, kModeScoreCk = 1, kModeTb = 2 };
 
-constexpr int kCH = 16;       // steps between the warps' counter updates
+constexpr int kCH = 8;        // steps between the warps' counter updates (it sets the lag between warps)
 constexpr int kQS = 256;      // boundary-ring columns per channel
 constexpr int kQB = 1024;     // residue-ring columns
 constexpr int kIOB = 64;      // columns per I/O batch
@@ -239,7 +239,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
 }
 
 template <int R, int W, int MODE, bool FOLD>
-__global__ void __launch_bounds__((W + 1) * 32) __maxnreg__(R >= 16 ? 128 : 96)
+__global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 16 ? 128 : 96)
 wavefront_kernel(const FillLaunch L)
 {
     constexpr int HC = W * 32 * R;
@@ -258,7 +258,6 @@ wavefront_kernel(const FillLaunch L)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const bool io = (warp == W);
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -299,11 +298,46 @@ wavefront_kernel(const FillLaunch L)
         }
         __syncthreads();
 
-        if (io) {
-            // ================= I/O warp =================
-            int in_next = 0, out_next = 0;
+        if (warp == W) {
+            // ================= input warp: top boundary row and residues =================
+            int in_next = 0;
             long long idle = 0;
             const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
+            const int *pprev = L.prog + (tk - 1);
+            int avail_prev = strip == 0 ? n : 0;
+            while (in_next < n) {
+                // room in channel 0 (consumer: warp 0) and in the residue ring
+                // (slowest reader: warp Wa-1, whose lane 31 is at column prod[Wa])
+                const int room0 = lds_acquire(&cons[0]) + QS;
+                const int roomb = lds_acquire(&prod[Wa]) + QB - 64;
+                int target = min(n, min(in_next + IOB, min(room0, roomb)));
+                if (target > in_next && strip > 0 && avail_prev < target)
+                    avail_prev = ld_acquire(pprev);              // every lane: acquire for its own loads
+                target = min(target, avail_prev);
+                if (target > in_next) {
+                    for (int col = in_next + lane; col < target; col += 32) {
+                        const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
+                        ring[0][col & (QS - 1)] = make_int2(v.x - go, v.y);
+                        bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
+                    }
+                    __syncwarp();
+                    if (lane == 0) sts_release(&prod[0], target);
+                    in_next = target;
+                    idle = 0;
+                } else {
+                    if (s_abort) break;
+                    if (++idle > L.spin_limit) {
+                        if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
+                        s_abort = 1;
+                        break;
+                    }
+                    if (idle > 32) __nanosleep(32);
+                }
+            }
+        } else if (warp == W + 1) {
+            // ================= output warp: bottom row to global memory =================
+            int out_next = 0;
+            long long idle = 0;
             // a checkpoint row only where the strip's bottom row lies inside the task
             // (the last strip may be partial)
             const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
@@ -312,34 +346,7 @@ wavefront_kernel(const FillLaunch L)
             // the last strip's bottom row feeds no other strip
             const bool store = strip + 1 < T.nstrips;
             int2 *dst = store ? T.bnd + (size_t)(strip % T.nslot) * n : nullptr;
-            const int *pprev = L.prog + (tk - 1);
-            int avail_prev = strip == 0 ? n : 0;
             while (out_next < n) {
-                bool moved = false;
-                if (in_next < n) {
-                    // room in channel 0 (consumer: warp 0) and in the residue ring
-                    // (slowest reader: warp W-1, whose lane 31 is at column prod[W])
-                    const int room0 = lds_acquire(&cons[0]) + QS;
-                    const int roomb = lds_acquire(&prod[Wa]) + QB - 64;
-                    int target = min(n, min(in_next + IOB, min(room0, roomb)));
-                    if (target > in_next && strip > 0 && avail_prev < target) {
-                        int v = 0;
-                        if (lane == 0) v = ld_acquire(pprev);
-                        avail_prev = __shfl_sync(kFull, v, 0);
-                    }
-                    target = min(target, avail_prev);
-                    if (target > in_next) {
-                        for (int col = in_next + lane; col < target; col += 32) {
-                            const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
-                            ring[0][col & (QS - 1)] = make_int2(v.x - go, v.y);
-                            bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
-                        }
-                        __syncwarp();
-                        if (lane == 0) sts_release(&prod[0], target);
-                        in_next = target;
-                        moved = true;
-                    }
-                }
                 const int avail_out = lds_acquire(&prod[Wa]);
                 if (avail_out > out_next) {
                     if (store || ck) {
@@ -349,17 +356,15 @@ wavefront_kernel(const FillLaunch L)
                             if (store) dst[col] = v;
                             if (ck) cdst[col] = v;
                         }
-                        __threadfence();
                     }
+                    // the lanes' stores are ordered before lane 0's release by the warp
+                    // barrier; the release (gpu scope) publishes them cumulatively
                     __syncwarp();
                     if (lane == 0) {
                         if (store) st_release(L.prog + tk, avail_out);
                         sts_release(&cons[Wa], avail_out);
                     }
                     out_next = avail_out;
-                    moved = true;
-                }
-                if (moved) {
                     idle = 0;
                 } else {
                     if (s_abort) break;
@@ -368,7 +373,7 @@ wavefront_kernel(const FillLaunch L)
                         s_abort = 1;
                         break;
                     }
-                    __nanosleep(64);
+                    if (idle > 32) __nanosleep(32);
                 }
             }
         } else if (warp >= Wa) {
@@ -404,6 +409,10 @@ wavefront_kernel(const FillLaunch L)
             int2 *rout = ring[warp + 1];
 
             int seen_in = 0;
+            bool loaded = false;             // inputs of step s0 were prefetched by the previous step
+            int c;
+            uint32_t pw[R / 4];
+            int2 top;
             for (int s0 = 0; s0 < n + 31; s0 += CH) {
                 const int need_in = min(n, s0 + CH + 1);   // this chunk plus the next step's prefetch
                 if (need_in > seen_in) {
@@ -412,15 +421,17 @@ wavefront_kernel(const FillLaunch L)
                 }
                 const int out_hi = min(n, max(0, s0 + CH - 31));
                 if (out_hi > 0 && !warp_wait_geq(&cons[warp + 1], out_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
-                // inputs of the chunk's first step
-                int j = s0 - lane;
-                int c = ((unsigned)j < (unsigned)n) ? min((int)bring[j & (QB - 1)], K) : K;
-                uint32_t pw[R / 4];
-                load_profile<R>(prow + c * HC, pw);
-                int2 top = rin[s0 & (QS - 1)];
+                if (!loaded) {
+                    // inputs of the sweep's first step (later steps prefetch the next one)
+                    const int j = s0 - lane;
+                    c = ((unsigned)j < (unsigned)n) ? min((int)bring[j & (QB - 1)], K) : K;
+                    load_profile<R>(prow + c * HC, pw);
+                    top = rin[s0 & (QS - 1)];
+                    loaded = true;
+                }
                 if (s0 >= 31 && s0 + CH + 1 <= n) {
                     // steady state: every lane's column and the prefetched one are in [0, n)
-#pragma unroll 4
+#pragma unroll
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
                         const int cn = min((int)bring[(s + 1 - lane) & (QB - 1)], K);
@@ -442,7 +453,7 @@ wavefront_kernel(const FillLaunch L)
                         const int jn = s + 1 - lane;
                         const int cn = ((unsigned)jn < (unsigned)n) ? min((int)bring[jn & (QB - 1)], K) : K;
                         load_profile<R>(prow + cn * HC, pw);
-                        top = rin[(s + 1) & (QS - 1)];
+                        top = rin[(s + 1) & (QS - 1)];   // stale when s + 1 >= n: lane 0 skips that column
                     }
                 }
                 __syncwarp();
