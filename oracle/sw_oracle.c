@@ -25,8 +25,9 @@
  *
  * Canonical outputs (the paper is silent on ties; these are this project's
  * readings):
- *   end cell   : the maximum H; among equal maxima the smallest column j
- *                (b_end), then the smallest row i (a_end).  Score 0 gives an
+ *   end cell   : the maximum H; among equal maxima the smallest row i
+ *                (a_end), then the smallest column j (b_end): the first in
+ *                row-major order, a down the rows.  Score 0 gives an
  *                empty alignment with every coordinate 0.
  *   traceback  : from the end cell in state H:
  *                  state H: stop if H(i,j) == 0; else diagonal if
@@ -65,8 +66,8 @@ static int better_end(int64_t h, int64_t i, int64_t j,
                       int64_t best, int64_t bi, int64_t bj)
 {
     if (h != best) return h > best;
-    if (j != bj) return j < bj;
-    return i < bi;
+    if (i != bi) return i < bi;
+    return j < bj;
 }
 
 /*

@@ -62,7 +62,7 @@ def brute_force(a, b, S, go, ge):
 
     Returns (score, a_end, b_end, canonical) where canonical is
     (a_begin, b_begin, ops) or None for score 0.  The end cell is the
-    smallest column then smallest row among optimal alignments; the
+    smallest row then smallest column among optimal alignments; the
     canonical alignment is the optimal one ending there whose backward
     walk is lexicographically smallest by rank (see backward_moves).
     """
@@ -76,7 +76,7 @@ def brute_force(a, b, S, go, ge):
             cands.append((i0, j0, i1, j1, ops))
     if best == 0:
         return 0, 0, 0, None
-    j_end, i_end = min((c[3], c[2]) for c in cands)
+    i_end, j_end = min((c[2], c[3]) for c in cands)
     at_end = [c for c in cands if c[2] == i_end and c[3] == j_end]
     canon = min(at_end, key=lambda c: backward_moves(c[4]))
     return best, i_end, j_end, (canon[0], canon[1], canon[4])

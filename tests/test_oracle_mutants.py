@@ -23,8 +23,8 @@ MUTANTS = [
      "int64_t H = Hdiag + S[b[j - 1] * K + a[i - 1]];"),
     ("dropped zero floor (score)", "            H = max2(H, 0);\n            Frow[j] = F;",
      "            Frow[j] = F;"),
-    ("row-major end tie-break", "    if (j != bj) return j < bj;\n    return i < bi;",
-     "    if (i != bi) return i < bi;\n    return j < bj;"),
+    ("column-major end tie-break", "    if (i != bi) return i < bi;\n    return j < bj;",
+     "    if (j != bj) return j < bj;\n    return i < bi;"),
     ("wrong diagonal index (full)", "int64_t h = AT(H, i - 1, j - 1) + S[a[i - 1] * K + b[j - 1]];",
      "int64_t h = AT(H, i - 1, j) + S[a[i - 1] * K + b[j - 1]];"),
     ("E opens with extend (full traceback)", "if (AT(E, i, j) == AT(H, i, j - 1) - o) state = 0;",
