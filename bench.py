@@ -41,6 +41,9 @@ INT_LANES_PER_SM = 128          # 4 sub-partitions x 32 integer lanes
 SM_MAX_MHZ = 2070.0
 OPS_PER_CELL = 10               # E: 2 sub + max, F: 2 sub + max, H: add + 3 max (incl. 0), running max
 WORKLOAD = "dna_pair_200kbp_align"
+# DRAM traffic of the forward fill measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) per cell, and the kernel source it was taken on.
+FILL_TRAFFIC = None
 
 
 def parse():
@@ -162,6 +165,7 @@ def run_swgb(args, rank, world):
 
     clocks = ClockSampler(dev)
     clocks.start()
+    ctx.timing(True)                 # per-kernel device time on the context stream
     launches0 = ctx.launches()
     times = []
     torch.cuda.synchronize()
@@ -177,6 +181,9 @@ def run_swgb(args, rank, world):
         assert aln == ref_aln
     torch.cuda.synchronize()
     launches = ctx.launches() - launches0
+    kt = {name: ctx.kernel_time(kind) for name, kind in
+          (("fill", binding.KT_FILL), ("fill_tb", binding.KT_FILL_TB), ("walk", binding.KT_WALK))}
+    ctx.timing(False)
     total = sum(times)
     if world > 1:
         t = torch.tensor([total], dtype=torch.float64, device="cuda")
@@ -207,7 +214,11 @@ def run_swgb(args, rank, world):
     d2h = 48 + len(aln.cigar)
 
     peak_ops = SM_COUNT_GB300 * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    fill_t = statistics.mean(fill_times)
+    score_t = statistics.mean(fill_times)
+    # the dominant kernel: the forward fill (one launch per step), timed by
+    # events recorded around its launches inside the timed steps
+    fill_ms, fill_n = kt["fill"]
+    fill_t = fill_ms / 1e3 / max(1, fill_n)
     achieved = OPS_PER_CELL * cells / fill_t
     probe = {}
     if not args.no_extras:
@@ -235,17 +246,38 @@ def run_swgb(args, rank, world):
         "gpu_launches": launches,
         "e2e": {"value": round(cells / statistics.median(e2e) / 1e9, 2), "unit": "GCUPS",
                 "h2d_bytes_per_step": m + n, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "kernel": "wavefront_kernel (forward fill, score mode)",
+        "roofline": {"bound": "alu",
+                     "kernel": "wavefront_kernel, forward fill (%s mode)" % (
+                         "checkpoint" if args.mode == "align" else "score"),
                      "achieved": round(achieved / 1e12, 3), "peak": round(peak_ops / 1e12, 3),
-                     "unit": "Tint-op/s", "frac": round(achieved / peak_ops, 4), "traffic": None,
+                     "unit": "Tint-op/s", "frac": round(achieved / peak_ops, 4),
+                     "traffic": fill_traffic(m, n, args.mode),
                      "ops_per_cell": OPS_PER_CELL, "fill_ms": round(1e3 * fill_t, 3),
-                     "fill_gcups": round(cells / fill_t / 1e9, 2),
-                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz"},
+                     "fill_launches": fill_n, "fill_gcups": round(cells / fill_t / 1e9, 2),
+                     "score_call_gcups": round(cells / score_t / 1e9, 2),
+                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (plain integer ALU issue)"},
+        "kernel_ms_per_step": {k: round(v[0] / max(1, args.steps), 3) for k, v in kt.items()},
         "clocks": clk,
     }
     if probe:
         out["roofline"]["measured_int_rates_per_sm_clk"] = probe
     return out
+
+
+def fill_traffic(m, n, mode):
+    """DRAM bytes (read + write) of one forward-fill launch, from the ncu
+    capture summarised in profiles/wavefront_fill_dna_pair.md, scaled by
+    cells; None once the kernel source differs from the profiled one."""
+    if FILL_TRAFFIC is None or mode != FILL_TRAFFIC["mode"]:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("wavefront.cuh", "sw_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2211_10769_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != FILL_TRAFFIC["source_sha256"]:
+        return None
+    return int(FILL_TRAFFIC["bytes_per_cell"] * m * n)
 
 
 def run_reference(args, rank, world):

@@ -22,8 +22,8 @@
  *   H(0,*) = H(*,0) = 0
  *
  * Canonical results (the paper is silent on ties):
- *   - end cell: the maximum H; among equal maxima the smallest column (b_end)
- *     and then the smallest row (a_end);
+ *   - end cell: the maximum H; among equal maxima the smallest row (a_end)
+ *     and then the smallest column (b_end), i.e. the first in row-major order;
  *   - traceback from the end cell: in H prefer the diagonal, then E, then F,
  *     stop where H = 0; inside a gap leave it (open) before extending it;
  *   - coordinates are 0-based, begin inclusive, end exclusive; score 0 means
@@ -275,6 +275,27 @@ void sw_server_destroy(sw_server *srv);
  * for a null context.
  */
 int64_t sw_ctx_launches(const sw_ctx *ctx);
+
+/*
+ * Kernel timing (instrumentation; the paper has no counterpart).  While
+ * enabled, the context records a CUDA event pair on its stream around every
+ * launch of the kernels below and accumulates their device time, so a
+ * caller can time one kernel class inside a longer call (for example the
+ * forward fill inside sw_align) without a profiler.  Launches issued while
+ * the stream is being captured into a CUDA graph are not timed.
+ *
+ * sw_ctx_timing: enable (1) or disable (0); either clears the totals.
+ * sw_ctx_kernel_time: total device milliseconds and launch count of one
+ *   kind since timing was enabled; waits for the recorded events.
+ *   SW_EINVAL for a null context, a bad kind or null outputs.
+ */
+#define SW_KT_FILL     0   /* wavefront fill, score and checkpoint modes (sw_score, sw_align forward, rescoring) */
+#define SW_KT_FILL_TB  1   /* wavefront fill, traceback mode (sw_align recompute) */
+#define SW_KT_WALK     2   /* traceback walk (sw_align) */
+#define SW_KT_DB16     3   /* packed 16-bit database fill (sw_dbsearch, server) */
+#define SW_KT_COUNT    4
+int sw_ctx_timing(sw_ctx *ctx, int32_t enable);
+int sw_ctx_kernel_time(sw_ctx *ctx, int32_t kind, double *ms, int64_t *launches);
 
 #ifdef __cplusplus
 }

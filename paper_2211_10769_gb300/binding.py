@@ -75,6 +75,8 @@ def load():
     lib.sw_alignment_free.restype = None
     lib.sw_ctx_launches.argtypes = [vp]
     lib.sw_ctx_launches.restype = i64
+    lib.sw_ctx_timing.argtypes = [vp, i32]
+    lib.sw_ctx_kernel_time.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.sw_db_create.argtypes = [vp, vp, vp, i64, ctypes.POINTER(vp)]
     lib.sw_db_destroy.argtypes = [vp]
     lib.sw_db_destroy.restype = None
@@ -187,6 +189,18 @@ class Context:
         """Kernels launched by this context so far."""
         return int(self._lib.sw_ctx_launches(self.handle))
 
+    def timing(self, enable: bool = True) -> None:
+        """Start (or stop) per-kernel device timing; clears the totals."""
+        _check(self._lib.sw_ctx_timing(self.handle, 1 if enable else 0), "sw_ctx_timing")
+
+    def kernel_time(self, kind: int):
+        """(total device ms, launches) of one kernel kind (KT_*) since timing() was enabled."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self._lib.sw_ctx_kernel_time(self.handle, kind, ctypes.byref(ms), ctypes.byref(n)),
+               "sw_ctx_kernel_time")
+        return ms.value, n.value
+
     def encode(self, alphabet: str, text) -> np.ndarray:
         raw = text.encode("ascii") if isinstance(text, str) else bytes(text)
         buf = np.frombuffer(raw, dtype=np.uint8).copy()
@@ -220,6 +234,7 @@ class Context:
 
 
 SW_BATCH_GRAPH, SW_BATCH_AUTOTUNE = 1, 2
+KT_FILL, KT_FILL_TB, KT_WALK, KT_DB16 = 0, 1, 2, 3     # kernel kinds of Context.kernel_time
 
 
 def _pack_pairs(pairs):

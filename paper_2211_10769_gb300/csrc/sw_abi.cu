@@ -126,7 +126,7 @@ int swgb::map_kernel_error(int e) {
 namespace {
 
 template <int R, int W, int MODE, bool FOLD>
-int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
+int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int max_blocks) {
     auto kern = wavefront_kernel<R, W, MODE, FOLD>;
     constexpr int HC = W * 32 * R;
     const size_t smem = (size_t)(K + 1) * HC;
@@ -139,29 +139,100 @@ int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets) {
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (W + 2) * 32, smem));
     if (occ < 1) return SW_ECUDA;
+    if (max_blocks > 0) occ = std::min(occ, max_blocks);
     const long long grid = std::min<long long>(tickets, (long long)occ * c->nsm);
+    const int kp = kt_begin(c, MODE == kModeTb ? SW_KT_FILL_TB : SW_KT_FILL);
     kern<<<(unsigned)grid, (W + 2) * 32, smem, c->stream>>>(L);
+    kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
     return SW_OK;
 }
 
 template <int R, int W>
-int launch_fill_rw(sw_ctx *c, int mode, bool fold, const FillLaunch &L, int K, long long tickets) {
+int launch_fill_rw(sw_ctx *c, int mode, bool fold, const FillLaunch &L, int K, long long tickets, int B) {
     switch (mode * 2 + (fold ? 1 : 0)) {
-        case 0: return launch_fill_cfg<R, W, kModeScore, false>(c, L, K, tickets);
-        case 1: return launch_fill_cfg<R, W, kModeScore, true>(c, L, K, tickets);
-        case 2: return launch_fill_cfg<R, W, kModeScoreCk, false>(c, L, K, tickets);
-        case 3: return launch_fill_cfg<R, W, kModeScoreCk, true>(c, L, K, tickets);
-        case 4: return launch_fill_cfg<R, W, kModeTb, false>(c, L, K, tickets);
-        case 5: return launch_fill_cfg<R, W, kModeTb, true>(c, L, K, tickets);
+        case 0: return launch_fill_cfg<R, W, kModeScore, false>(c, L, K, tickets, B);
+        case 1: return launch_fill_cfg<R, W, kModeScore, true>(c, L, K, tickets, B);
+        case 2: return launch_fill_cfg<R, W, kModeScoreCk, false>(c, L, K, tickets, B);
+        case 3: return launch_fill_cfg<R, W, kModeScoreCk, true>(c, L, K, tickets, B);
+        case 4: return launch_fill_cfg<R, W, kModeTb, false>(c, L, K, tickets, B);
+        case 5: return launch_fill_cfg<R, W, kModeTb, true>(c, L, K, tickets, B);
         default: return SW_EINVAL;
     }
 }
 
 }  // namespace
 
+// ------------------------------------------------------------- kernel timing
+
+void swgb::KernelTimer::destroy() {
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+    ev.clear();
+    kind.clear();
+}
+
+namespace {
+
+// Adds the recorded pairs to the totals; waits for the last recorded event.
+int kt_fold(sw_ctx *c) {
+    KernelTimer &T = c->timer;
+    const size_t np = T.kind.size();
+    if (np == 0) return SW_OK;
+    CU(cudaEventSynchronize(T.ev[2 * (np - 1) + 1]));
+    for (size_t k = 0; k < np; ++k) {
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, T.ev[2 * k], T.ev[2 * k + 1]));
+        T.ms[T.kind[k]] += ms;
+        T.n[T.kind[k]] += 1;
+    }
+    T.kind.clear();
+    return SW_OK;
+}
+
+}  // namespace
+
+int swgb::kt_begin(sw_ctx *c, int kind) {
+    KernelTimer &T = c->timer;
+    if (!T.on) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) { cudaGetLastError(); return -1; }
+    if (cs != cudaStreamCaptureStatusNone) return -1;
+    if (T.ev.empty()) {
+        T.ev.assign(2 * KernelTimer::kPairs, nullptr);
+        for (cudaEvent_t &e : T.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); T.destroy(); T.on = false; return -1; }
+    }
+    if ((int)T.kind.size() == KernelTimer::kPairs && kt_fold(c) != SW_OK) return -1;
+    const int p = (int)T.kind.size();
+    if (cudaEventRecord(T.ev[2 * p], c->stream) != cudaSuccess) { cudaGetLastError(); return -1; }
+    T.kind.push_back(kind);
+    return p;
+}
+
+void swgb::kt_end(sw_ctx *c, int p) {
+    if (p < 0) return;
+    if (cudaEventRecord(c->timer.ev[2 * p + 1], c->stream) != cudaSuccess) cudaGetLastError();
+}
+
+// ------------------------------------------------------------- tile shapes
+
 int swgb::fill_rows_per_strip(const FillConfig &cfg) { return cfg.W * 32 * cfg.R; }
+
+// Compute warps per strip for a fill of one pair with `rows` rows.  The strips
+// of a pair form a chain (each waits on the bottom row of the one above), so
+// the chain runs at the pace of its slowest strip: two strips sharing an SM
+// slow the whole pair.  Take the fewest warps (at least 4, where a strip's
+// step is still latency-bound) that give at most one strip per SM; all W
+// when even that many strips outnumber the SMs.
+int swgb::pair_strip_warps(const sw_ctx *c, const FillConfig &cfg, int64_t rows) {
+    if (cfg.S > 0) return std::min(cfg.S, cfg.W);
+    for (int w = std::min(4, cfg.W); w < cfg.W; ++w) {
+        const int64_t sh = (int64_t)w * 32 * cfg.R;
+        if ((rows + sh - 1) / sh <= (int64_t)c->nsm) return w;
+    }
+    return cfg.W;
+}
 
 bool swgb::fold_open(const DevScoring &s) {
     int lo = 127, hi = -128;
@@ -172,10 +243,10 @@ bool swgb::fold_open(const DevScoring &s) {
 int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                       long long tickets) {
     if (tickets <= 0) return SW_OK;
-    if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets);
-    if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets);
-    if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets);
-    if (cfg.R == 16 && cfg.W == 4) return launch_fill_rw<16, 4>(c, mode, fold, L, K, tickets);
+    if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets, cfg.B);
+    if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets, cfg.B);
+    if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets, cfg.B);
+    if (cfg.R == 16 && cfg.W == 4) return launch_fill_rw<16, 4>(c, mode, fold, L, K, tickets, cfg.B);
     return SW_EINVAL;
 }
 
@@ -283,11 +354,13 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     }
     const char *ev = std::getenv("SWGB_SPIN_LIMIT");
     c->spin_limit = ev ? std::atoll(ev) : (1LL << 26);
-    c->fwd = FillConfig{8, 4};
+    c->fwd = FillConfig{8, 4, 0, 2};
     c->tbc = FillConfig{8, 4};
-    // tuning overrides: SWGB_FWD="R,W" and SWGB_TB="R,W" (tile shapes of the fills)
-    if (const char *f = std::getenv("SWGB_FWD")) std::sscanf(f, "%d,%d", &c->fwd.R, &c->fwd.W);
+    c->bat = FillConfig{8, 4};
+    // tuning overrides: SWGB_FWD="R,W[,S[,B]]", SWGB_TB="R,W" and SWGB_BATCH="R,W" (tile shapes of the fills)
+    if (const char *f = std::getenv("SWGB_FWD")) std::sscanf(f, "%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B);
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
+    if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
     c->ckpt_budget = (size_t)4 << 30;
     c->tb_budget = (size_t)4 << 30;
     *out = c;
@@ -361,11 +434,13 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
 
-    const int HC = fill_rows_per_strip(c->fwd);
+    const int sw = pair_strip_warps(c, c->fwd, m);
+    const int SH = sw * 32 * c->fwd.R;
     FillTask t{};
     t.a = da; t.b = db;
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
-    t.nstrips = (int32_t)((m + HC - 1) / HC);
+    t.strip_warps = sw;
+    t.nstrips = (int32_t)((m + SH - 1) / SH);
     t.scoring = 0; t.ticket0 = 0;
     t.top = nullptr;
     t.nslot = std::min(t.nstrips, 4);
@@ -394,6 +469,24 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
 }
 
 int64_t sw_ctx_launches(const sw_ctx *c) { return c ? c->launches : -1; }
+
+int sw_ctx_timing(sw_ctx *c, int32_t enable) {
+    if (!c) return SW_EINVAL;
+    KernelTimer &T = c->timer;
+    T.kind.clear();
+    for (int k = 0; k < SW_KT_COUNT; ++k) { T.ms[k] = 0; T.n[k] = 0; }
+    T.on = enable != 0;
+    return SW_OK;
+}
+
+int sw_ctx_kernel_time(sw_ctx *c, int32_t kind, double *ms, int64_t *launches) {
+    if (!c || kind < 0 || kind >= SW_KT_COUNT || !ms || !launches) return SW_EINVAL;
+    DeviceGuard g(c->device);
+    RC(kt_fold(c));
+    *ms = c->timer.ms[kind];
+    *launches = c->timer.n[kind];
+    return SW_OK;
+}
 
 void sw_alignment_free(sw_alignment *aln) {
     if (!aln) return;

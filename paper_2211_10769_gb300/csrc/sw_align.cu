@@ -23,6 +23,7 @@
 #include "aux_kernels.cuh"
 
 #include <algorithm>
+#include <numeric>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -51,8 +52,10 @@ int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, i
     TileTable<Word> T;
     T.bits = reinterpret_cast<const Word *const *>(table);
     T.I0 = I0; T.J0 = J0; T.nI = nI; T.nJ = nJ; T.BT = BT; T.R = R;
+    const int kp = kt_begin(c, SW_KT_WALK);
     walk_kernel<Word><<<1, 32, 0, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
                                                 static_cast<int2 *>(c->runs.p), kWalkMaxIters);
+    kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
     return SW_OK;
@@ -89,21 +92,26 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     const bool fold = fold_open(ds);
 
     // ---- tile side: both checkpoint sets within the budget
-    const int HC = fill_rows_per_strip(c->fwd);
+    // tiles are BT x BT; BT is a multiple of both fills' strip heights, so
+    // checkpoint rows fall on forward-strip bottoms and tiles hold whole
+    // traceback strips
+    const int sw = pair_strip_warps(c, c->fwd, m);
+    const int HC = sw * 32 * c->fwd.R;
     const int HT = fill_rows_per_strip(c->tbc);
-    long long BT = std::max(HC, HT);
-    BT = std::max(BT, 1024LL);
+    const long long BL = std::lcm((long long)HC, (long long)HT);
+    long long BT = BL * ((1024 + BL - 1) / BL);
     auto ck_bytes = [&](long long bt) {
         return (size_t)((m / bt) * n + (n / bt) * m) * sizeof(int2);
     };
     while (ck_bytes(BT) > c->ckpt_budget && BT < (1LL << 30)) BT *= 2;
-    if (BT % HC != 0 || BT % HT != 0) return SW_EINVAL;
+    if (BT % HC != 0 || BT % HT != 0 || BT > (1LL << 30)) return SW_EINVAL;
     const long long nrowck = std::max<long long>(1, m / BT), ncolck = std::max<long long>(1, n / BT);
 
     // ---- 1. forward fill with row and column checkpoints
     FillTask t{};
     t.a = da; t.b = db;
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
+    t.strip_warps = sw;
     t.nstrips = (int32_t)((m + HC - 1) / HC);
     t.scoring = 0; t.ticket0 = 0; t.top = nullptr; t.left = nullptr; t.corner = nullptr; t.row0 = 0;
     t.nslot = std::min(t.nstrips, 4);

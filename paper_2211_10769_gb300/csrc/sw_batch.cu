@@ -283,7 +283,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
     }
     // tile shape: cached for the size class, else autotuned (or the context default)
     const long long cls = size_class(B);
-    FillConfig cfg = c->fwd;
+    FillConfig cfg = c->bat;
     bool tuned = false;
     for (const auto &kv : c->batch_tune)
         if (kv.first == cls) { cfg = kv.second; tuned = true; }

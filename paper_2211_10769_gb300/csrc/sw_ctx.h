@@ -35,10 +35,28 @@ struct DeviceGuard {
     ~DeviceGuard();
 };
 
-// Tile shape of the wavefront fill: R rows per lane, W compute warps.
+// Tile shape of the wavefront fill: R rows per lane, W compute warps per
+// block; S fixes the compute warps per strip of a single-pair fill (0 = chosen
+// from the pair's length); B caps the resident blocks per SM (0 = as many as
+// fit).
 struct FillConfig {
     int R;
     int W;
+    int S = 0;
+    int B = 0;
+};
+
+// Device time per kernel kind (sw_ctx_timing): event pairs recorded around
+// launches, folded into totals when read or when the pool is full.
+struct KernelTimer {
+    static constexpr int kPairs = 4096;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;      // 2 * kPairs, created on first use
+    std::vector<int> kind;            // kind of each recorded pair
+    double ms[SW_KT_COUNT] = {};
+    long long n[SW_KT_COUNT] = {};
+    void destroy();
+    ~KernelTimer() { destroy(); }
 };
 
 }  // namespace swgb
@@ -49,14 +67,16 @@ struct sw_ctx {
     int nsm = 0;
     long long spin_limit = 0;
     long long launches = 0;           // kernels launched by this context
-    swgb::FillConfig fwd{8, 4};       // score / forward pass
+    swgb::FillConfig fwd{8, 4, 0, 2}; // score / forward pass
     swgb::FillConfig tbc{8, 4};       // traceback recompute
+    swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
     swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, tb,
         tbbnd, runs, walk, misc, dbscratch, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
     std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class
+    swgb::KernelTimer timer;
 };
 
 namespace swgb {
@@ -67,12 +87,15 @@ int max_pos_score(const sw_scoring *sc);
 int stage_seq(sw_ctx *c, const uint8_t *p, int64_t len, DevBuf &buf, const uint8_t **dptr);
 int map_kernel_error(int e);
 int fill_rows_per_strip(const FillConfig &cfg);
+int pair_strip_warps(const sw_ctx *c, const FillConfig &cfg, int64_t rows);
 bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
 int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                 long long tickets);
 int run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const std::vector<FillTask> &tasks,
              long long tickets, int K);
 int upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s);
+int kt_begin(sw_ctx *c, int kind);         // -1 when not timing; else the pair to close with kt_end
+void kt_end(sw_ctx *c, int pair);
 int reset_err(sw_ctx *c);
 int validate_codes(sw_ctx *c, const uint8_t *d, int64_t len, int K);
 int read_err(sw_ctx *c, int *e);

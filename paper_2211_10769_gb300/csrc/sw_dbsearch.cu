@@ -49,9 +49,11 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     const size_t smem = (size_t)(K + 1) * (size_t)mpad;
     // boundary rows: one per warp
     RC(c->dbscratch.ensure((size_t)nblocks * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    const int kp = kt_begin(c, SW_KT_DB16);
     kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
                                                          static_cast<const DevScoring *>(c->scorings.p),
                                                          static_cast<uint2 *>(c->dbscratch.p));
+    kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
     return SW_OK;
@@ -258,7 +260,7 @@ int swgb::db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, c
                      const std::vector<int32_t> &flagged, int32_t *dscores) {
     const int K = ds.K;
     RC(upload_scorings(c, {ds}));
-    const int HC = fill_rows_per_strip(c->fwd);
+    const int HC = fill_rows_per_strip(c->bat);
     std::vector<FillTask> tasks;
     tasks.reserve(flagged.size());
     long long tickets = 0;
@@ -286,7 +288,7 @@ int swgb::db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, c
         if (n == 0) { u.nstrips = 0; }
         tasks.push_back(u);
     }
-    RC(run_fill(c, c->fwd, kModeScore, fold_open(ds), tasks, tickets, K));
+    RC(run_fill(c, c->bat, kModeScore, fold_open(ds), tasks, tickets, K));
     const int nt = (int)tasks.size();
     RC(c->result.ensure((size_t)nt * sizeof(int4)));
     reduce_candidates_kernel<<<(nt + 7) / 8, 256, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), nt,

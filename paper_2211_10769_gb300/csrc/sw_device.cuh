@@ -49,12 +49,12 @@ __device__ __forceinline__ int ld_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-// Lexicographic order of end-cell candidates: larger score, then smaller
-// column j, then smaller row i.
+// Order of end-cell candidates: larger score, then smaller row i, then
+// smaller column j (the first maximum in row-major order).
 __device__ __forceinline__ bool cand_better(int s1, int j1, int i1, int s2, int j2, int i2) {
     if (s1 != s2) return s1 > s2;
-    if (j1 != j2) return j1 < j2;
-    return i1 < i2;
+    if (i1 != i2) return i1 < i2;
+    return j1 < j2;
 }
 
 }  // namespace swgb

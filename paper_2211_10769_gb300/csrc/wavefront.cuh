@@ -6,7 +6,8 @@
 // against columns [0, ncols) of its `b` slice, entered from a top boundary
 // row (H, F per column; the matrix border when null) and a left boundary
 // column (H, E per row; the matrix border when null).  It is cut into
-// strips of HC = W*32*R rows; one thread block computes one strip at a time.
+// strips of strip_warps*32*R rows (at most HC = W*32*R); one thread block
+// computes one strip at a time.
 //
 //   * Each of the W compute warps owns 32*R consecutive rows, each lane R
 //     of them in registers.  Lanes form an anti-diagonal wavefront: at warp
@@ -34,7 +35,7 @@
 // c = K at -128), one vector load and one prmt per cell.
 //
 // Modes: score (TB = false) keeps, per lane, the best H with its first
-// column, then first row, and writes one end-cell candidate per strip; it
+// row, then first column, and writes one end-cell candidate per strip; it
 // can also store the strip's bottom row as a checkpoint row and, every
 // `colck_every` columns, the (H, E) column as a checkpoint column.
 // Traceback (TB = true) writes, for every cell, four decision bits
@@ -60,7 +61,7 @@ struct FillTask {
                            // written by the last strip; may be null for one-strip tasks)
     int32_t nslot;
     int32_t ckpt_every;    // also copy every ckpt_every-th strip's bottom row to ckpt (0 = never);
-                           // only strips whose bottom row is inside the task: rows / (HC * ckpt_every) rows
+                           // only strips whose bottom row is inside the task: rows / (strip rows * ckpt_every) rows
     int2 *ckpt;            // checkpoint rows: ((strip+1)/ckpt_every - 1) * ncols
     int2 *colck;           // checkpoint columns (H, E): (c/colck_every - 1) * colck_ld + row
     int32_t colck_every;   // 0 = none; else store after every colck_every-th column
@@ -68,6 +69,8 @@ struct FillTask {
     int64_t colck_ld;
     void *tb;              // traceback words, TB mode: [row group][tb_ld]
     int64_t tb_ld;
+    int32_t strip_warps;   // compute warps per strip (rows per strip = strip_warps * 32 * R);
+                           // 0 = all W warps of the block
 };
 
 struct FillLaunch {
@@ -151,23 +154,32 @@ struct LaneState {
     int U[R], E[R];
     int ub, fb, udiag0;
     int best, bj, br;
+    int thr;         // a column maximum above thr may replace the best (see resolve_pending)
     int cm;          // column maximum of the previous step
-    int pending;     // the previous step's column beat `best`; resolved at the next step
+    int pending;     // the previous step's column may beat the best; resolved at the next step
     int next_ck;
 };
 
-// Record the previous step's improvement: best column j - 1 and its first row
-// reaching the maximum (U still holds that column).  Taken at the start of
-// a step, so the branch condition is ready long before it is needed.
+// The lane's end cell is the first of its cells in row-major order holding
+// its maximum.  Columns arrive in order, so a later column replaces the best
+// when its maximum is larger, or equal and first reached in an earlier row;
+// thr is best when the best sits in the lane's first row (only a larger
+// value can win) and best - 1 otherwise, which makes the per-step test one
+// comparison.  The test is resolved at the start of the next step (U still
+// holds that column), so the branch condition is ready long before it is
+// needed.
 template <int R>
 __device__ __forceinline__ void resolve_pending(LaneState<R> &st, int jprev) {
     if (st.pending) {
-        st.best = st.cm;
-        st.bj = jprev;
         int rr = R - 1;
 #pragma unroll
         for (int r = R - 1; r >= 0; --r) if (st.U[r] == st.cm) rr = r;
-        st.br = rr;
+        if (st.cm > st.best || rr < st.br) {
+            st.best = st.cm;
+            st.bj = jprev;
+            st.br = rr;
+            st.thr = rr > 0 ? st.cm - 1 : st.cm;
+        }
         st.pending = 0;
     }
 }
@@ -225,7 +237,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
         for (int r = 1; r + 1 < R; r += 2) cm = __vimax3_s32(cm, st.U[r], st.U[r + 1]);
         if constexpr (R % 2 == 0) cm = max(cm, st.U[R - 1]);
         st.cm = cm;
-        st.pending = cm > st.best;
+        st.pending = cm > st.thr;
         if constexpr (MODE == kModeScoreCk) {
             if (j == st.next_ck) {
                 int2 *cc = colck + (size_t)((j + 1) / colck_every - 1) * (size_t)colck_ld;
@@ -282,13 +294,15 @@ wavefront_kernel(const FillLaunch L)
         const DevScoring &SC = L.scorings[T.scoring];
         const int K = SC.K, go = SC.go, ge = SC.ge;
         const int strip = (int)(tk - T.ticket0);
-        const int rbase = strip * HC;                   // first row of the strip within the task
+        const int SW = (T.strip_warps > 0 && T.strip_warps < W) ? T.strip_warps : W;
+        const int SH = SW * 32 * R;                     // rows per strip of this task
+        const int rbase = strip * SH;                   // first row of the strip within the task
         const int n = T.ncols;
         // warps holding at least one row of the task; the others sit the strip out
-        const int Wa = min(W, (T.rows - rbase + 32 * R - 1) / (32 * R));
+        const int Wa = min(SW, (T.rows - rbase + 32 * R - 1) / (32 * R));
 
         // ---- query profile of the strip's rows: S(a_r, c) (+ open when folded)
-        for (int lr = threadIdx.x; lr < HC; lr += blockDim.x) {
+        for (int lr = threadIdx.x; lr < SH; lr += blockDim.x) {
             const int r = rbase + lr;
             const bool ok = r < T.rows;
             const int av = ok ? min((int)T.a[r], K - 1) : 0;
@@ -341,7 +355,7 @@ wavefront_kernel(const FillLaunch L)
             // a checkpoint row only where the strip's bottom row lies inside the task
             // (the last strip may be partial)
             const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
-                            (long long)(strip + 1) * HC <= (long long)T.rows;
+                            (long long)(strip + 1) * SH <= (long long)T.rows;
             int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
             // the last strip's bottom row feeds no other strip
             const bool store = strip + 1 < T.nstrips;
@@ -398,7 +412,7 @@ wavefront_kernel(const FillLaunch L)
             if (grow == 0) hcorner = T.corner ? __ldcg(T.corner).x : 0;
             else hcorner = (T.left && grow - 1 < T.rows) ? __ldcg(T.left + grow - 1).x : 0;
             st.udiag0 = hcorner - go;
-            st.best = -go; st.bj = -1; st.br = 0; st.cm = -go; st.pending = 0;
+            st.best = -go; st.bj = -1; st.br = 0; st.thr = -go; st.cm = -go; st.pending = 0;
             const int colck_every = (MODE == kModeScoreCk) ? T.colck_every : 0;
             st.next_ck = colck_every > 0 ? colck_every - 1 : 0x7fffffff;
             int2 *colck = (MODE == kModeScoreCk && T.colck) ? T.colck + (T.row0 + grow) : nullptr;

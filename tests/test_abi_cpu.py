@@ -46,6 +46,17 @@ def test_strerror_without_gpu(lib):
     assert lib.sw_strerror(-1) == b"invalid argument"
 
 
+def test_null_context_arguments_without_gpu(lib):
+    """Calls that only inspect their arguments reject a null context."""
+    lib.sw_ctx_timing.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.sw_ctx_kernel_time.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.sw_ctx_launches.argtypes = [ctypes.c_void_p]
+    lib.sw_ctx_launches.restype = ctypes.c_int64
+    assert lib.sw_ctx_timing(None, 1) == -1
+    assert lib.sw_ctx_kernel_time(None, 0, None, None) == -1
+    assert lib.sw_ctx_launches(None) == -1
+
+
 def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     from paper_2211_10769_gb300 import binding
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "absent.so"))

@@ -218,3 +218,52 @@ def test_align_paths_cross_tiles(ctx, oracle_mod, case):
     assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
         (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end)
     assert got.cigar == want.cigar
+
+
+@pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1"])
+def test_strip_heights(oracle_mod, monkeypatch, fwd):
+    """Forward strips of 1280, 1536, 768 and 512 rows: strip bottoms, row
+    checkpoints and traceback tiles (sides that are multiples of both strip
+    heights) must still meet exactly."""
+    from paper_2211_10769_gb300 import binding, build
+    build.build()
+    monkeypatch.setenv("SWGB_FWD", fwd)
+    c = binding.Context(0)
+    try:
+        seed = W.BASE_SEED + 9700
+        A, B = _long_gap_pair(seed, 13000, 4100, 6900, insert=False)
+        S = np.full((4, 4), -4, np.int8)
+        np.fill_diagonal(S, 5)
+        for (a, b, o, e) in [(A, B, 20, 1), (A[:7000], W.mutate(A[:7000], 4, seed + 5, p_sub=0.1, p_indel=0.02), 5, 2)]:
+            want = oracle_mod.sw_align_ptr(a, b, S, o, e)
+            got = c.align(a, b, S, o, e)
+            assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+                (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end), fwd
+            assert got.cigar == want.cigar, fwd
+            h = c.score(a, b, S, o, e)
+            assert (h.score, h.a_end, h.b_end) == (want.score, want.a_end, want.b_end), fwd
+    finally:
+        c.close()
+
+
+def test_kernel_timing(ctx):
+    """Per-kernel device time: one forward fill per sw_align, walks and
+    traceback fills counted, totals cleared when timing is re-enabled."""
+    from paper_2211_10769_gb300 import binding
+    sc = W.dna_scoring()
+    a, b = W.dna_pair_2k()
+    ctx.timing(True)
+    for _ in range(3):
+        ctx.align(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    ms, n = ctx.kernel_time(binding.KT_FILL)
+    assert n == 3 and ms > 0
+    ms_tb, n_tb = ctx.kernel_time(binding.KT_FILL_TB)
+    ms_w, n_w = ctx.kernel_time(binding.KT_WALK)
+    assert n_tb >= 3 and n_w == n_tb and ms_tb > 0 and ms_w > 0
+    ctx.timing(True)
+    assert ctx.kernel_time(binding.KT_FILL) == (0.0, 0)
+    ctx.timing(False)
+    ctx.score(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    assert ctx.kernel_time(binding.KT_FILL) == (0.0, 0)
+    with pytest.raises(binding.SwError):
+        ctx.kernel_time(7)
