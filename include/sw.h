@@ -137,8 +137,9 @@ int sw_encode(sw_ctx *ctx, const char *alphabet, const char *text, int64_t len, 
 /*
  * Resolution phase for one pair (paper Section 2.2): best local score and
  * its canonical end cell.  0 <= m, n <= SW_MAX_LEN; every code < alphabet.
- * Scores must fit in int32 (|score| <= min(m,n) * max|S| < 2^31), else
- * SW_ERANGE.
+ * Scores are bounded by min(m, n) * max S(x, y), which must be below 2^26
+ * (67,108,864), else SW_ERANGE (the int32 fill tags row indices into the
+ * low bits of its scores to pick the canonical end cell without branches).
  */
 int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
              const sw_scoring *sc, sw_hit *out);

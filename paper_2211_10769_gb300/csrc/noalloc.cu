@@ -90,7 +90,7 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     const long long nstrips = (m + kHC - 1) / kHC;
     if (n > kMaxCols || nstrips > kMaxStrips) return SW_ERANGE;
-    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
     if (m == 0 || n == 0) { *out = sw_hit{0, 0, 0, 0}; return SW_OK; }
     if (!is_device_ptr(a) || !is_device_ptr(b)) return SW_EINVAL;   // inputs must already be on the device
     int dev = 0;

@@ -423,7 +423,7 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(check_scoring(sc, &ds));
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
-    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
     if (m == 0 || n == 0) { *out = sw_hit{0, 0, 0, 0}; return SW_OK; }
     DeviceGuard g(c->device);
     const uint8_t *da, *db;

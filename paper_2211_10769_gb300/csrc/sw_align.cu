@@ -79,7 +79,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(check_scoring(sc, &ds));
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
-    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
     if (m == 0 || n == 0) return empty_alignment(out);
     DeviceGuard g(c->device);
     const uint8_t *da, *db;

@@ -227,7 +227,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
         int mx = 0;
         const DevScoring &d = B->scorings[(size_t)scoring_of_pair[p]];
         for (int k = 0; k < d.K * d.K; ++k) mx = std::max(mx, (int)d.mat[k]);
-        if ((double)std::min(m, n) * (double)mx >= (double)(1 << 30)) return SW_ERANGE;
+        if ((double)std::min(m, n) * (double)mx >= (double)kMaxScoreBound) return SW_ERANGE;
         B->m[(size_t)p] = m;
         B->n[(size_t)p] = n;
     }

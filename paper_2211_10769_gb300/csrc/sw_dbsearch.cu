@@ -338,7 +338,7 @@ extern "C" int sw_dbsearch(sw_ctx *c, const sw_db *db, const uint8_t *q, int64_t
     if (m < 0 || (m > 0 && !q)) return SW_EINVAL;
     if (m > SW_MAX_LEN) return SW_ERANGE;
     if (db->max_code >= ds.K) return SW_EINVAL;
-    if ((double)std::min<int64_t>(m, db->maxlen) * (double)max_pos_score(sc) >= (double)(1 << 30)) return SW_ERANGE;
+    if ((double)std::min<int64_t>(m, db->maxlen) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
     DeviceGuard g(c->device);
     const int64_t nseq = db->nseq;
     RC(c->dbscores.ensure((size_t)std::max<int64_t>(1, nseq) * sizeof(int32_t)));

@@ -8,6 +8,9 @@
 namespace swgb {
 
 constexpr int kNeg = -(1 << 30);      // stands for -infinity in int32 lanes
+// Scores of the int32 fill stay below this bound (min(m, n) * max S < it):
+// the fill keys rows as U * 16 + tag, which must not overflow int32.
+constexpr long long kMaxScoreBound = 1LL << 26;
 constexpr int kPadScore = -128;       // profile value of padding rows / columns
 constexpr int kMaxAlphabet = 32;
 constexpr unsigned kFull = 0xffffffffu;

@@ -35,7 +35,8 @@
 // c = K at -128), one vector load and one prmt per cell.
 //
 // Modes: score (TB = false) keeps, per lane, the best H with its first
-// row, then first column, and writes one end-cell candidate per strip; it
+// row, then first column (a branch-free row key, see row_key), and writes
+// one end-cell candidate per strip; it
 // can also store the strip's bottom row as a checkpoint row and, every
 // `colck_every` columns, the (H, E) column as a checkpoint column.
 // Traceback (TB = true) writes, for every cell, four decision bits
@@ -147,42 +148,29 @@ constexpr int kIOB = 64;      // columns per I/O batch
 // Per-lane state of the sweep.  U = H - open and E of the lane's R rows at
 // the previous column; ub / fb the bottom row's U and F of the previous step
 // (shuffled to the next lane); udiag0 = U of the row above the first row at
-// the previous column (the first row's diagonal); the best U so far with
-// its column and row.
+// the previous column (the first row's diagonal); bk / bj the lane's best
+// cell as a row key (below) and its column.
 template <int R>
 struct LaneState {
     int U[R], E[R];
     int ub, fb, udiag0;
-    int best, bj, br;
-    int thr;         // a column maximum above thr may replace the best (see resolve_pending)
-    int cm;          // column maximum of the previous step
-    int pending;     // the previous step's column may beat the best; resolved at the next step
+    int bk, bj;
     int next_ck;
 };
 
 // The lane's end cell is the first of its cells in row-major order holding
-// its maximum.  Columns arrive in order, so a later column replaces the best
-// when its maximum is larger, or equal and first reached in an earlier row;
-// thr is best when the best sits in the lane's first row (only a larger
-// value can win) and best - 1 otherwise, which makes the per-step test one
-// comparison.  The test is resolved at the start of the next step (U still
-// holds that column), so the branch condition is ready long before it is
-// needed.
+// its maximum.  Each row r of a column gets the key U * kKeyRows + (R-1-r):
+// one integer maximum over the rows then picks the largest U and, among
+// equal ones, the smallest row.  Columns arrive in order, so a column
+// replaces the lane's best exactly when its key is strictly larger (a larger
+// score, or an equal one in an earlier row): one compare and two selects per
+// step, no branch.  Keys need |U| < 2^31 / kKeyRows (callers bound scores by
+// kMaxScoreBound).
+constexpr int kKeyRows = 16;
+static_assert(kKeyRows * kMaxScoreBound <= (1LL << 30), "row keys overflow");
+
 template <int R>
-__device__ __forceinline__ void resolve_pending(LaneState<R> &st, int jprev) {
-    if (st.pending) {
-        int rr = R - 1;
-#pragma unroll
-        for (int r = R - 1; r >= 0; --r) if (st.U[r] == st.cm) rr = r;
-        if (st.cm > st.best || rr < st.br) {
-            st.best = st.cm;
-            st.bj = jprev;
-            st.br = rr;
-            st.thr = rr > 0 ? st.cm - 1 : st.cm;
-        }
-        st.pending = 0;
-    }
-}
+__device__ __forceinline__ int row_key(int u, int r) { return u * kKeyRows + (R - 1 - r); }
 
 // One wavefront step of one lane: column j = s - lane of its R rows.
 // CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
@@ -198,7 +186,6 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     int uup = __shfl_up_sync(kFull, st.ub, 1);
     int fup = __shfl_up_sync(kFull, st.fb, 1);
     if (lane == 0) { uup = top.x; fup = top.y; }
-    if constexpr (MODE != kModeTb) resolve_pending(st, j - 1);
     if (CHECK && (j < 0 || j >= n)) return;
     int udiag = st.udiag0;
     st.udiag0 = uup;
@@ -232,12 +219,13 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     if constexpr (MODE == kModeTb) {
         tbw[j] = word;
     } else {
-        int cm = st.U[0];
+        int ck = row_key<R>(st.U[0], 0);
 #pragma unroll
-        for (int r = 1; r + 1 < R; r += 2) cm = __vimax3_s32(cm, st.U[r], st.U[r + 1]);
-        if constexpr (R % 2 == 0) cm = max(cm, st.U[R - 1]);
-        st.cm = cm;
-        st.pending = cm > st.thr;
+        for (int r = 1; r + 1 < R; r += 2)
+            ck = __vimax3_s32(ck, row_key<R>(st.U[r], r), row_key<R>(st.U[r + 1], r + 1));
+        if constexpr (R % 2 == 0) ck = max(ck, row_key<R>(st.U[R - 1], R - 1));
+        st.bj = ck > st.bk ? j : st.bj;
+        st.bk = max(st.bk, ck);
         if constexpr (MODE == kModeScoreCk) {
             if (j == st.next_ck) {
                 int2 *cc = colck + (size_t)((j + 1) / colck_every - 1) * (size_t)colck_ld;
@@ -412,7 +400,7 @@ wavefront_kernel(const FillLaunch L)
             if (grow == 0) hcorner = T.corner ? __ldcg(T.corner).x : 0;
             else hcorner = (T.left && grow - 1 < T.rows) ? __ldcg(T.left + grow - 1).x : 0;
             st.udiag0 = hcorner - go;
-            st.best = -go; st.bj = -1; st.br = 0; st.thr = -go; st.cm = -go; st.pending = 0;
+            st.bk = row_key<R>(-go, 0); st.bj = -1;      // score 0 never becomes the best
             const int colck_every = (MODE == kModeScoreCk) ? T.colck_every : 0;
             st.next_ck = colck_every > 0 ? colck_every - 1 : 0x7fffffff;
             int2 *colck = (MODE == kModeScoreCk && T.colck) ? T.colck + (T.row0 + grow) : nullptr;
@@ -478,9 +466,10 @@ wavefront_kernel(const FillLaunch L)
             }
 
             if constexpr (MODE != kModeTb) {
-                resolve_pending(st, n - 1);    // only lane 31 can hold one: its last step was column n - 1
-                int cs = st.best + go, cj = st.bj + 1, ci = T.row0 + grow + st.br + 1;
-                if (cs <= 0 || grow + st.br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
+                const int br = R - 1 - (st.bk & (kKeyRows - 1));
+                int cs = (st.bk >> 4) + go, cj = st.bj + 1, ci = T.row0 + grow + br + 1;
+                static_assert(kKeyRows == 16, "key decode assumes 4 row bits");
+                if (cs <= 0 || grow + br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const int os = __shfl_xor_sync(kFull, cs, off);
