@@ -219,6 +219,24 @@ void swgb::kt_end(sw_ctx *c, int p) {
 
 int swgb::fill_rows_per_strip(const FillConfig &cfg) { return cfg.W * 32 * cfg.R; }
 
+int swgb::tb_word_bytes(int R) { return R <= 4 ? 2 : (R <= 8 ? 4 : 8); }
+
+// Tile shape of a single-pair fill of `rows` rows.  A pair's strips form one
+// chain (each waits on the bottom row of the one above), so the chain runs
+// at the pace of its slowest strip, and a strip that shares an SM with
+// another runs at about half its pace.  Four compute warps (one per SM
+// sub-partition) with the fewest rows per lane R that still give at most one
+// strip per SM: a smaller R shortens the step's dependency chain.  Pairs too
+// tall for that take R = 16 and two strips per SM.
+FillConfig swgb::pair_fill_config(const sw_ctx *c, int64_t rows) {
+    if (!c->fwd_auto) return c->fwd;
+    for (int R : {4, 8, 12, 16}) {
+        const int64_t sh = 4LL * 32 * R;
+        if ((rows + sh - 1) / sh <= (int64_t)c->nsm) return FillConfig{R, 4, 0, 2};
+    }
+    return FillConfig{16, 4, 0, 2};
+}
+
 // Compute warps per strip for a fill of one pair with `rows` rows.  The strips
 // of a pair form a chain (each waits on the bottom row of the one above), so
 // the chain runs at the pace of its slowest strip: two strips sharing an SM
@@ -246,6 +264,7 @@ int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, con
     if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets, cfg.B);
+    if (cfg.R == 12 && cfg.W == 4) return launch_fill_rw<12, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 16 && cfg.W == 4) return launch_fill_rw<16, 4>(c, mode, fold, L, K, tickets, cfg.B);
     return SW_EINVAL;
 }
@@ -358,7 +377,10 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     c->tbc = FillConfig{8, 4};
     c->bat = FillConfig{8, 4};
     // tuning overrides: SWGB_FWD="R,W[,S[,B]]", SWGB_TB="R,W" and SWGB_BATCH="R,W" (tile shapes of the fills)
-    if (const char *f = std::getenv("SWGB_FWD")) std::sscanf(f, "%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B);
+    if (const char *f = std::getenv("SWGB_FWD")) {
+        std::sscanf(f, "%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B);
+        c->fwd_auto = false;
+    }
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
     c->ckpt_budget = (size_t)4 << 30;
@@ -434,8 +456,9 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
 
-    const int sw = pair_strip_warps(c, c->fwd, m);
-    const int SH = sw * 32 * c->fwd.R;
+    const FillConfig fwd = pair_fill_config(c, m);
+    const int sw = pair_strip_warps(c, fwd, m);
+    const int SH = sw * 32 * fwd.R;
     FillTask t{};
     t.a = da; t.b = db;
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
@@ -447,7 +470,7 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
     t.bnd = static_cast<int2 *>(c->bnd.p);
     t.ckpt_every = 0; t.ckpt = nullptr; t.row0 = 0; t.tb = nullptr; t.tb_ld = 0;
-    RC(run_fill(c, c->fwd, kModeScore, fold_open(ds), {t}, t.nstrips, ds.K));
+    RC(run_fill(c, fwd, kModeScore, fold_open(ds), {t}, t.nstrips, ds.K));
 
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,

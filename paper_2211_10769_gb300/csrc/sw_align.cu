@@ -4,12 +4,16 @@
 //
 // 1. Forward fill over the whole matrix (score mode with checkpoints): the
 //    H / F row at every BT-th row and the H / E column at every BT-th
-//    column are kept.  BT is a power of two chosen so that both sets of
-//    checkpoints fit the checkpoint budget, so memory is O((m + n)^2 / BT)
-//    rather than m x n.
+//    column are kept.  BT is the smallest multiple of both fills' strip
+//    heights (at least 1024) for which both sets of checkpoints fit the
+//    checkpoint budget, so memory is O((m + n)^2 / BT) rather than m x n.
+//    The columns are stored in staircase form (each lane of the fill one
+//    column further left than the lane above it, all at one step, so the
+//    sweep needs no per-step test); a tile entered from one first brings its
+//    lanes to the straight column (see FillTask::left).
 // 2. The end cell (ie, je) comes from the per-strip candidates.
 // 3. With checkpoints on both sides, every BT x BT tile can be recomputed
-//    on its own from its top row, left column and corner.  The walk goes
+//    on its own from its top row and left column.  The walk goes
 //    in rounds: recompute the decision bits of a diagonal band of tiles
 //    from the walk's current tile towards the upper left (traceback mode,
 //    every tile an independent task of one launch), walk the path through
@@ -65,6 +69,7 @@ int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int
     switch (R) {
         case 4: return launch_walk_t<uint16_t>(c, table, I0, J0, nI, nJ, BT, R);
         case 8: return launch_walk_t<uint32_t>(c, table, I0, J0, nI, nJ, BT, R);
+        case 12:
         case 16: return launch_walk_t<unsigned long long>(c, table, I0, J0, nI, nJ, BT, R);
         default: return SW_EINVAL;
     }
@@ -95,9 +100,13 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     // tiles are BT x BT; BT is a multiple of both fills' strip heights, so
     // checkpoint rows fall on forward-strip bottoms and tiles hold whole
     // traceback strips
-    const int sw = pair_strip_warps(c, c->fwd, m);
-    const int HC = sw * 32 * c->fwd.R;
-    const int HT = fill_rows_per_strip(c->tbc);
+    const FillConfig fwd = pair_fill_config(c, m);
+    const int sw = pair_strip_warps(c, fwd, m);
+    const int HC = sw * 32 * fwd.R;
+    // the traceback tiles continue the forward fill's staircase checkpoint columns lane by
+    // lane, so both fills must give each lane the same rows (R)
+    const FillConfig tbc = c->tbc.R == fwd.R ? c->tbc : FillConfig{fwd.R, 4};
+    const int HT = fill_rows_per_strip(tbc);
     const long long BL = std::lcm((long long)HC, (long long)HT);
     long long BT = BL * ((1024 + BL - 1) / BL);
     auto ck_bytes = [&](long long bt) {
@@ -113,7 +122,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
     t.strip_warps = sw;
     t.nstrips = (int32_t)((m + HC - 1) / HC);
-    t.scoring = 0; t.ticket0 = 0; t.top = nullptr; t.left = nullptr; t.corner = nullptr; t.row0 = 0;
+    t.scoring = 0; t.ticket0 = 0; t.top = nullptr; t.left = nullptr; t.left_aux = nullptr; t.row0 = 0;
     t.nslot = std::min(t.nstrips, 4);
     RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
     t.bnd = static_cast<int2 *>(c->bnd.p);
@@ -121,10 +130,12 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->ckpt.ensure((size_t)nrowck * (size_t)n * sizeof(int2)));
     t.ckpt = static_cast<int2 *>(c->ckpt.p);
     t.colck_every = (int32_t)BT;
-    t.colck_ld = m;
-    RC(c->colck.ensure((size_t)ncolck * (size_t)m * sizeof(int2)));
+    t.colck_ld = (long long)t.nstrips * HC;     // rows padded to whole strips (the padding is written)
+    RC(c->colck.ensure((size_t)ncolck * (size_t)t.colck_ld * sizeof(int2)));
+    RC(c->colaux.ensure((size_t)ncolck * (size_t)(t.colck_ld / fwd.R) * sizeof(int2)));
     t.colck = static_cast<int2 *>(c->colck.p);
-    RC(run_fill(c, c->fwd, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
+    t.colck_aux = static_cast<int2 *>(c->colaux.p);
+    RC(run_fill(c, fwd, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,
                                                        static_cast<const int4 *>(c->cand.p),
@@ -154,14 +165,15 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     CU(cudaStreamSynchronize(c->stream));
 
     // ---- 3. rounds: recompute a band of tiles, walk through it
-    const int R = c->tbc.R;
+    const int R = tbc.R;
     const size_t tile_words = (size_t)(BT / R) * (size_t)BT;
-    const size_t tile_bytes = tile_words * (size_t)(R / 2);
+    const size_t tile_bytes = tile_words * (size_t)tb_word_bytes(R);
     const int maxtiles = 3 * kBandDepth;
     RC(c->tb.ensure(tile_bytes * maxtiles));
     RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
     RC(c->misc.ensure(table_cap * sizeof(void *)));
-    const int2 *rowck = t.ckpt, *colck = t.colck;
+    const int2 *rowck = t.ckpt, *colck = t.colck, *colaux = t.colck_aux;
+    const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / fwd.R;
     int prev_i = -1, prev_j = -1, prev_state = -1;
     while (true) {
         const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
@@ -184,8 +196,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.scoring = 0;
                 u.ticket0 = tickets;
                 u.top = ti > 0 ? rowck + (size_t)(ti - 1) * n + c0 : nullptr;
-                u.left = tj > 0 ? colck + (size_t)(tj - 1) * m + r0 : nullptr;
-                u.corner = (ti > 0 && tj > 0) ? colck + (size_t)(tj - 1) * m + r0 - 1 : nullptr;
+                u.left = tj > 0 ? colck + (size_t)(tj - 1) * colck_ld + r0 : nullptr;
+                u.left_aux = tj > 0 ? colaux + (size_t)(tj - 1) * colaux_ld + r0 / fwd.R : nullptr;
                 const size_t k = tasks.size();
                 u.nslot = std::min(u.nstrips, 2);
                 u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;
@@ -198,7 +210,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 table[(size_t)(ti - I0) * nJ + (tj - J0)] = u.tb;
             }
         }
-        RC(run_fill(c, c->tbc, kModeTb, fold, tasks, tickets, ds.K));
+        RC(run_fill(c, tbc, kModeTb, fold, tasks, tickets, ds.K));
         const size_t tbytes = table.size() * sizeof(void *);
         if (tbytes > c->stage2.cap) return SW_EINVAL;
         std::memcpy(c->stage2.p, table.data(), tbytes);

@@ -67,12 +67,13 @@ struct sw_ctx {
     int nsm = 0;
     long long spin_limit = 0;
     long long launches = 0;           // kernels launched by this context
-    swgb::FillConfig fwd{8, 4, 0, 2}; // score / forward pass
+    swgb::FillConfig fwd{8, 4, 0, 2}; // score / forward pass (when fwd_auto is false)
+    bool fwd_auto = true;             // choose R per pair (pair_fill_config)
     swgb::FillConfig tbc{8, 4};       // traceback recompute
     swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
-    swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, tb,
+    swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, colaux, tb,
         tbbnd, runs, walk, misc, dbscratch, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
     std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class
@@ -88,6 +89,8 @@ int stage_seq(sw_ctx *c, const uint8_t *p, int64_t len, DevBuf &buf, const uint8
 int map_kernel_error(int e);
 int fill_rows_per_strip(const FillConfig &cfg);
 int pair_strip_warps(const sw_ctx *c, const FillConfig &cfg, int64_t rows);
+FillConfig pair_fill_config(const sw_ctx *c, int64_t rows);
+int tb_word_bytes(int R);
 bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
 int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                 long long tickets);

@@ -48,6 +48,16 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+// Four (a, b) pairs stored to p[0..3] (32 bytes, 16-byte aligned) only when
+// pred != 0, as predicated instructions (no branch in the caller's stream).
+__device__ __forceinline__ void st_global_4x2_if(unsigned pred, int2 *p, int a0, int b0, int a1, int b1,
+                                                 int a2, int b2, int a3, int b3) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+                 "@q st.global.v4.s32 [%1], {%2, %3, %4, %5};\n\t"
+                 "@q st.global.v4.s32 [%1+16], {%6, %7, %8, %9};\n\t}"
+                 :: "r"(pred), "l"(p), "r"(a0), "r"(b0), "r"(a1), "r"(b1), "r"(a2), "r"(b2), "r"(a3), "r"(b3));
+}
+
 __device__ __forceinline__ int ld_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }

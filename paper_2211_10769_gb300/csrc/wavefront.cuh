@@ -36,9 +36,11 @@
 //
 // Modes: score (TB = false) keeps, per lane, the best H with its first
 // row, then first column (a branch-free row key, see row_key), and writes
-// one end-cell candidate per strip; it
-// can also store the strip's bottom row as a checkpoint row and, every
-// `colck_every` columns, the (H, E) column as a checkpoint column.
+// one end-cell candidate per strip; it can also store the strip's bottom row
+// as a checkpoint row and, every `colck_every` columns, a checkpoint column
+// in staircase form (all lanes store at one step, so lane l's rows hold
+// column c - l; a task entered from such a column first brings every lane to
+// column c, see FillTask::left).
 // Traceback (TB = true) writes, for every cell, four decision bits
 // {H source: 0 zero, 1 diagonal, 2 E, 3 F; E opened; F opened} packed R
 // nibbles per word, for the walk.
@@ -56,15 +58,20 @@ struct FillTask {
     int32_t scoring;       // index into the scoring table
     int64_t ticket0;       // global ticket of strip 0
     const int2 *top;       // (H, F) per column of the row above, or null (matrix border)
-    const int2 *left;      // (H, E) per row of the column to the left, or null (matrix border)
-    const int2 *corner;    // H of the cell above-left in .x, or null (0)
+    const int2 *left;      // staircase left boundary, or null (matrix border): row i of 32-lane
+                           // group lane l = (i / R) % 32 holds (H - open, E) at column c - l,
+                           // c = the column left of the task (written by a kModeScoreCk fill)
+    const int2 *left_aux;  // per row group of left: (H - open of the row above at column c - l,
+                           // F of the group's last row at column c - l)
     int2 *bnd;             // bottom rows of the strips: slot (strip % nslot) * ncols (not
                            // written by the last strip; may be null for one-strip tasks)
     int32_t nslot;
     int32_t ckpt_every;    // also copy every ckpt_every-th strip's bottom row to ckpt (0 = never);
                            // only strips whose bottom row is inside the task: rows / (strip rows * ckpt_every) rows
     int2 *ckpt;            // checkpoint rows: ((strip+1)/ckpt_every - 1) * ncols
-    int2 *colck;           // checkpoint columns (H, E): (c/colck_every - 1) * colck_ld + row
+    int2 *colck;           // checkpoint columns, staircase form (see left): checkpoint k = (c+1)/colck_every - 1
+                           // at colck + k * colck_ld + row; colck_ld covers the last strip's padding rows
+    int2 *colck_aux;       // the matching left_aux rows: colck_aux + k * (colck_ld / R) + row / R
     int32_t colck_every;   // 0 = none; else store after every colck_every-th column
     int32_t row0;          // row index (0-based, in the whole pair) of the task's first row
     int64_t colck_ld;
@@ -89,6 +96,7 @@ struct FillLaunch {
 template <int R> struct TbWord;
 template <> struct TbWord<4> { using T = uint16_t; };
 template <> struct TbWord<8> { using T = uint32_t; };
+template <> struct TbWord<12> { using T = unsigned long long; };
 template <> struct TbWord<16> { using T = unsigned long long; };
 
 template <int R>
@@ -98,6 +106,9 @@ __device__ __forceinline__ void load_profile(const int8_t *p, uint32_t (&w)[R / 
     } else if constexpr (R == 8) {
         const uint2 v = *reinterpret_cast<const uint2 *>(p);
         w[0] = v.x; w[1] = v.y;
+    } else if constexpr (R == 12) {           // 12-byte lane stride: 4-byte aligned only
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
+        w[0] = q[0]; w[1] = q[1]; w[2] = q[2];
     } else {
         const uint4 v = *reinterpret_cast<const uint4 *>(p);
         w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
@@ -155,7 +166,6 @@ struct LaneState {
     int U[R], E[R];
     int ub, fb, udiag0;
     int bk, bj;
-    int next_ck;
 };
 
 // The lane's end cell is the first of its cells in row-major order holding
@@ -172,26 +182,18 @@ static_assert(kKeyRows * kMaxScoreBound <= (1LL << 30), "row keys overflow");
 template <int R>
 __device__ __forceinline__ int row_key(int u, int r) { return u * kKeyRows + (R - 1 - r); }
 
-// One wavefront step of one lane: column j = s - lane of its R rows.
-// CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
-// a sweep); the steady state skips those tests.
-template <int R, int MODE, bool FOLD, bool CHECK>
-__device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[R / 4], int2 top,
-                                          int s, int lane, int n, int go, int ge,
-                                          int2 *ring_out, typename TbWord<R>::T *tbw,
-                                          int2 *colck, long long colck_ld, int colck_every,
-                                          int grow, int rows)
+// One column of one lane's R rows (Gotoh recurrence, paper Section 2.1.2),
+// entered with uup / fup = H - open and F of the row above at this column;
+// st.udiag0 holds H - open of the row above at the previous column.  TB
+// collects the four decision bits of every cell into word.
+template <int R, bool FOLD, bool TB>
+__device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (&pw)[R / 4], int uup, int fup,
+                                              int go, int ge, typename TbWord<R>::T &word)
 {
-    const int j = s - lane;
-    int uup = __shfl_up_sync(kFull, st.ub, 1);
-    int fup = __shfl_up_sync(kFull, st.fb, 1);
-    if (lane == 0) { uup = top.x; fup = top.y; }
-    if (CHECK && (j < 0 || j >= n)) return;
     int udiag = st.udiag0;
     st.udiag0 = uup;
     int f = __viaddmax_s32(fup, -ge, uup);                 // F of the first row
     int fopen_ref = uup;                                   // H(i-1,j) - open
-    typename TbWord<R>::T word = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int sp = score_byte(pw, r);                        // S (+ open when folded)
@@ -201,7 +203,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
         const int x = __viaddmax_s32_relu(udiag, sp, e);   // max(H(i-1,j-1) + S, E, 0)
         const int xgo = x - go;
         const int u = __viaddmax_s32(f, -go, xgo);         // H(i,j) - open
-        if constexpr (MODE == kModeTb) {
+        if constexpr (TB) {
             const int h = u + go, diag = udiag + sp;
             const unsigned src = h == 0 ? 0u : (h == diag ? 1u : (h == e ? 2u : 3u));
             const unsigned nib = src | (e == uold ? 4u : 0u) | (f == fopen_ref ? 8u : 0u);
@@ -215,6 +217,23 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     }
     st.ub = st.U[R - 1];
     st.fb = f;
+}
+
+// One wavefront step of one lane: column j = s - lane of its R rows.
+// CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
+// a sweep); the steady state skips those tests.
+template <int R, int MODE, bool FOLD, bool CHECK>
+__device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[R / 4], int2 top,
+                                          int s, int lane, int n, int go, int ge,
+                                          int2 *ring_out, typename TbWord<R>::T *tbw)
+{
+    const int j = s - lane;
+    int uup = __shfl_up_sync(kFull, st.ub, 1);
+    int fup = __shfl_up_sync(kFull, st.fb, 1);
+    if (lane == 0) { uup = top.x; fup = top.y; }
+    if (CHECK && (j < 0 || j >= n)) return;
+    typename TbWord<R>::T word = 0;
+    column_update<R, FOLD, MODE == kModeTb>(st, pw, uup, fup, go, ge, word);
     if (lane == 31) ring_out[j & (kQS - 1)] = make_int2(st.ub, st.fb);
     if constexpr (MODE == kModeTb) {
         tbw[j] = word;
@@ -226,20 +245,11 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
         if constexpr (R % 2 == 0) ck = max(ck, row_key<R>(st.U[R - 1], R - 1));
         st.bj = ck > st.bk ? j : st.bj;
         st.bk = max(st.bk, ck);
-        if constexpr (MODE == kModeScoreCk) {
-            if (j == st.next_ck) {
-                int2 *cc = colck + (size_t)((j + 1) / colck_every - 1) * (size_t)colck_ld;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (grow + r < rows) cc[r] = make_int2(st.U[r] + go, st.E[r]);
-                st.next_ck += colck_every;
-            }
-        }
     }
 }
 
 template <int R, int W, int MODE, bool FOLD>
-__global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 16 ? 128 : 96)
+__global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 12 ? 128 : (W > 4 ? 96 : 104))
 wavefront_kernel(const FillLaunch L)
 {
     constexpr int HC = W * 32 * R;
@@ -388,22 +398,41 @@ wavefront_kernel(const FillLaunch L)
             const int8_t *prow = prof + lrow;
             LaneState<R> st;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                int h0 = 0, e0 = kNeg;
-                if (T.left && grow + r < T.rows) { const int2 v = __ldcg(T.left + grow + r); h0 = v.x; e0 = v.y; }
-                st.U[r] = h0 - go; st.E[r] = e0;
-            }
+            for (int r = 0; r < R; ++r) { st.U[r] = -go; st.E[r] = kNeg; }
+            st.udiag0 = -go;                                // matrix border: H = 0
             st.ub = st.U[R - 1];
             st.fb = kNeg;
-            // H of the row above this lane's first row, at the column left of the task
-            int hcorner;
-            if (grow == 0) hcorner = T.corner ? __ldcg(T.corner).x : 0;
-            else hcorner = (T.left && grow - 1 < T.rows) ? __ldcg(T.left + grow - 1).x : 0;
-            st.udiag0 = hcorner - go;
+            if (T.left) {
+                // Staircase left boundary: lane l's rows hold column c - l (c = the column
+                // left of the task).  Lane l advances l columns, in step with its neighbours
+                // (lane l's k-th column needs lane l-1's (k-1)-th), so that every lane ends at
+                // column c: a 31-step wavefront inside the warp.
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (grow + r < T.rows) { const int2 v = __ldcg(T.left + grow + r); st.U[r] = v.x; st.E[r] = v.y; }
+                const int2 ax = grow < T.rows ? __ldcg(T.left_aux + grow / R) : make_int2(-go, kNeg);
+                st.udiag0 = ax.x;
+                st.ub = st.U[R - 1];
+                st.fb = ax.y;
+                for (int k = 1; k < 32; ++k) {
+                    const int uup = __shfl_up_sync(kFull, st.ub, 1);
+                    const int fup = __shfl_up_sync(kFull, st.fb, 1);
+                    if (k <= lane) {
+                        const int cb = min((int)T.b[k - lane - 1], K);   // column c - lane + k
+                        uint32_t pwk[R / 4];
+                        load_profile<R>(prow + cb * HC, pwk);
+                        typename TbWord<R>::T unused = 0;
+                        column_update<R, FOLD, false>(st, pwk, uup, fup, go, ge, unused);
+                    }
+                }
+                // the diagonal of the task's first column: the row above at column c
+                const int up = __shfl_up_sync(kFull, st.ub, 1);
+                if (lane > 0) st.udiag0 = up;
+            }
             st.bk = row_key<R>(-go, 0); st.bj = -1;      // score 0 never becomes the best
-            const int colck_every = (MODE == kModeScoreCk) ? T.colck_every : 0;
-            st.next_ck = colck_every > 0 ? colck_every - 1 : 0x7fffffff;
-            int2 *colck = (MODE == kModeScoreCk && T.colck) ? T.colck + (T.row0 + grow) : nullptr;
+            // checkpoint columns (kModeScoreCk): every lane stores at the end of the chunk whose
+            // last step is column next_ck for lane 0, so lane l stores column next_ck - l
+            int next_ck = (MODE == kModeScoreCk && T.colck && T.colck_every > 0) ? T.colck_every - 1 : 0x7fffffff;
             typename TbWord<R>::T *tbw = nullptr;
             if constexpr (MODE == kModeTb)
                 tbw = reinterpret_cast<typename TbWord<R>::T *>(T.tb) + (size_t)(grow / R) * (size_t)T.tb_ld;
@@ -440,22 +469,37 @@ wavefront_kernel(const FillLaunch L)
                         const int2 topn = rin[(s + 1) & (QS - 1)];
                         uint32_t pwn[R / 4];
                         load_profile<R>(prow + cn * HC, pwn);
-                        lane_step<R, MODE, FOLD, false>(st, pw, top, s, lane, n, go, ge, rout, tbw,
-                                                        colck, T.colck_ld, colck_every, grow, T.rows);
+                        lane_step<R, MODE, FOLD, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
                         for (int q = 0; q < R / 4; ++q) pw[q] = pwn[q];
                         top = topn;
                     }
                 } else {
+                    // the first and last 31 steps: the same prefetch, bounds-checked
+#pragma unroll 1
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
                         if (s >= n + 31) break;
-                        lane_step<R, MODE, FOLD, true>(st, pw, top, s, lane, n, go, ge, rout, tbw,
-                                                       colck, T.colck_ld, colck_every, grow, T.rows);
                         const int jn = s + 1 - lane;
                         const int cn = ((unsigned)jn < (unsigned)n) ? min((int)bring[jn & (QB - 1)], K) : K;
-                        load_profile<R>(prow + cn * HC, pw);
-                        top = rin[(s + 1) & (QS - 1)];   // stale when s + 1 >= n: lane 0 skips that column
+                        const int2 topn = rin[(s + 1) & (QS - 1)];   // stale when s + 1 >= n: lane 0 skips that column
+                        uint32_t pwn[R / 4];
+                        load_profile<R>(prow + cn * HC, pwn);
+                        lane_step<R, MODE, FOLD, true>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+#pragma unroll
+                        for (int q = 0; q < R / 4; ++q) pw[q] = pwn[q];
+                        top = topn;
+                    }
+                }
+                if constexpr (MODE == kModeScoreCk) {
+                    if (s0 + CH - 1 == next_ck && next_ck < n) {   // the same for every lane
+                        const long long kk = (next_ck + 1) / T.colck_every - 1;
+                        int2 *cc = T.colck + kk * T.colck_ld + (T.row0 + grow);
+#pragma unroll
+                        for (int r = 0; r < R; r += 2)
+                            *reinterpret_cast<int4 *>(cc + r) = make_int4(st.U[r], st.E[r], st.U[r + 1], st.E[r + 1]);
+                        T.colck_aux[kk * (T.colck_ld / R) + (T.row0 + grow) / R] = make_int2(st.udiag0, st.fb);
+                        next_ck += T.colck_every;
                     }
                 }
                 __syncwarp();

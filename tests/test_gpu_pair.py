@@ -220,9 +220,9 @@ def test_align_paths_cross_tiles(ctx, oracle_mod, case):
     assert got.cigar == want.cigar
 
 
-@pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1"])
+@pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1", "12,4", "4,4"])
 def test_strip_heights(oracle_mod, monkeypatch, fwd):
-    """Forward strips of 1280, 1536, 768 and 512 rows: strip bottoms, row
+    """Forward strips of 1280, 1536, 768, 512, 1536 (12 rows a lane) and 512 rows: strip bottoms, row
     checkpoints and traceback tiles (sides that are multiples of both strip
     heights) must still meet exactly."""
     from paper_2211_10769_gb300 import binding, build
