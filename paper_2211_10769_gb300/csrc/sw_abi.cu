@@ -383,6 +383,8 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     }
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
+    if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
+    if (const char *f = std::getenv("SWGB_TB_SW")) c->tb_strip_warps = std::atoi(f);
     c->ckpt_budget = (size_t)4 << 30;
     c->tb_budget = (size_t)4 << 30;
     *out = c;

@@ -40,7 +40,7 @@ using namespace swgb;
 
 namespace {
 
-constexpr int kBandDepth = 16;            // tile rows per band (three tiles per tile row)
+constexpr int kMinBandDepth = 16;         // tile rows per band at least (three tiles per tile row)
 constexpr long long kWalkMaxIters = 1LL << 26;
 
 int empty_alignment(sw_alignment *out) {
@@ -51,14 +51,15 @@ int empty_alignment(sw_alignment *out) {
     return SW_OK;
 }
 
-template <typename Word>
-int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT, int R) {
+template <typename Word, int R>
+int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT) {
+    if ((long long)nI * nJ > kWalkTableMax || BT < 32 * kLook) return SW_EINVAL;
     TileTable<Word> T;
     T.bits = reinterpret_cast<const Word *const *>(table);
     T.I0 = I0; T.J0 = J0; T.nI = nI; T.nJ = nJ; T.BT = BT; T.R = R;
     const int kp = kt_begin(c, SW_KT_WALK);
-    walk_kernel<Word><<<1, 32, 0, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
-                                                static_cast<int2 *>(c->runs.p), kWalkMaxIters);
+    walk_kernel<Word, R><<<1, 32, 0, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
+                                                   static_cast<int2 *>(c->runs.p), kWalkMaxIters);
     kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
@@ -67,10 +68,10 @@ int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, i
 
 int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT, int R) {
     switch (R) {
-        case 4: return launch_walk_t<uint16_t>(c, table, I0, J0, nI, nJ, BT, R);
-        case 8: return launch_walk_t<uint32_t>(c, table, I0, J0, nI, nJ, BT, R);
-        case 12:
-        case 16: return launch_walk_t<unsigned long long>(c, table, I0, J0, nI, nJ, BT, R);
+        case 4: return launch_walk_t<uint16_t, 4>(c, table, I0, J0, nI, nJ, BT);
+        case 8: return launch_walk_t<uint32_t, 8>(c, table, I0, J0, nI, nJ, BT);
+        case 12: return launch_walk_t<unsigned long long, 12>(c, table, I0, J0, nI, nJ, BT);
+        case 16: return launch_walk_t<unsigned long long, 16>(c, table, I0, J0, nI, nJ, BT);
         default: return SW_EINVAL;
     }
 }
@@ -158,7 +159,11 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->walk.ensure(sizeof(WalkState)));
     RC(c->runs.ensure((size_t)(ie + je + 2) * sizeof(int2)));
     WalkState w{ie, je, 0, 0, 0, -1, 0};
-    const size_t table_cap = (size_t)(kBandDepth + 1) * (kBandDepth + 2);
+    // a band of three tiles per tile row, deep enough for about one tile per SM
+    const int band = c->tb_band > 0 ? std::min(c->tb_band, 60) : std::max(kMinBandDepth, c->nsm / 3);
+    const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
+    const int HS = tsw * 32 * tbc.R;                     // rows per traceback strip
+    const size_t table_cap = (size_t)(band + 1) * (band + 2);
     RC(c->stage2.ensure(std::max(sizeof(WalkState), table_cap * sizeof(void *))));
     std::memcpy(c->stage2.p, &w, sizeof(w));
     CU(cudaMemcpyAsync(c->walk.p, c->stage2.p, sizeof(w), cudaMemcpyHostToDevice, c->stream));
@@ -168,7 +173,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     const int R = tbc.R;
     const size_t tile_words = (size_t)(BT / R) * (size_t)BT;
     const size_t tile_bytes = tile_words * (size_t)tb_word_bytes(R);
-    const int maxtiles = 3 * kBandDepth;
+    const int maxtiles = 3 * band;
     RC(c->tb.ensure(tile_bytes * maxtiles));
     RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
     RC(c->misc.ensure(table_cap * sizeof(void *)));
@@ -177,12 +182,12 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     int prev_i = -1, prev_j = -1, prev_state = -1;
     while (true) {
         const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
-        const int I0 = std::max(0, I - kBandDepth + 1), J0 = std::max(0, J - kBandDepth);
+        const int I0 = std::max(0, I - band + 1), J0 = std::max(0, J - band);
         const int nI = I - I0 + 1, nJ = J - J0 + 1;
         std::vector<const void *> table((size_t)nI * nJ, nullptr);
         std::vector<FillTask> tasks;
         long long tickets = 0;
-        for (int d = 0; d < kBandDepth && I - d >= 0; ++d) {
+        for (int d = 0; d < band && I - d >= 0; ++d) {
             for (int dl = -1; dl <= 1; ++dl) {
                 const int ti = I - d, tj = J - d + dl;
                 if (tj < 0 || tj > J) continue;
@@ -192,7 +197,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.b = db + c0;
                 u.rows = (int32_t)std::min<long long>(BT, m - r0);
                 u.ncols = (int32_t)std::min<long long>(BT, n - c0);
-                u.nstrips = (u.rows + HT - 1) / HT;
+                u.strip_warps = tsw;
+                u.nstrips = (u.rows + HS - 1) / HS;
                 u.scoring = 0;
                 u.ticket0 = tickets;
                 u.top = ti > 0 ? rowck + (size_t)(ti - 1) * n + c0 : nullptr;

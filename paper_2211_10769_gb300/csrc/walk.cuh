@@ -10,11 +10,12 @@
 //   state E: emit I, go left; back to H if the E-opened bit is set;
 //   state F: emit D, go up; back to H if the F-opened bit is set.
 //
-// One warp walks.  Runs are taken 32 cells at a time: in state H the lanes
-// read the 32 cells of the diagonal ahead and the walk jumps over the
-// leading cells whose source is "diagonal"; in state E (F) they read the
-// 32 cells to the left (above) and the walk jumps to the first one whose
-// opened bit is set.  Only the run-ending cell is handled one at a time.
+// One warp walks.  Runs are taken 128 cells at a time (each lane issues
+// four loads at once, so their latencies overlap): in state H the lanes
+// read the cells of the diagonal ahead and the walk jumps over the leading
+// cells whose source is "diagonal"; in state E (F) they read the cells to
+// the left (above) and the walk jumps to the first one whose opened bit is
+// set.  Only the run-ending cell is handled one at a time.
 // The walk stops when it reaches a zero cell or the border (done = 1), or
 // when its next cell lies in a tile that was not recomputed this round
 // (done = 0, the host computes that tile next).
@@ -43,28 +44,48 @@ struct TileTable {
     int32_t R;                 // rows per word
 };
 
-template <typename Word>
-__device__ __forceinline__ const Word *tile_of(const TileTable<Word> &T, int i, int j) {
-    const int I = (i - 1) / T.BT - T.I0, J = (j - 1) / T.BT - T.J0;
-    if (I < 0 || J < 0 || I >= T.nI || J >= T.nJ) return nullptr;
-    return T.bits[I * T.nJ + J];
-}
+constexpr int kLook = 4;           // groups of 32 cells each lane reads ahead per iteration
+constexpr int kWalkTableMax = 4096;   // tile-table entries cached in shared memory
 
-// Decision nibble of cell (i, j) (1-based) inside its tile, or -1 if the tile is missing.
-template <typename Word>
-__device__ __forceinline__ int nibble_at(const TileTable<Word> &T, int i, int j) {
-    const Word *b = tile_of(T, i, j);
+// Where the walk is: its cell's tile (absolute tile row / column) and the
+// cell's offsets inside that tile.  One division per iteration.
+struct WalkPos {
+    int I, J, li, lj;
+};
+
+// Decision nibble of the cell p steps back along (di, dj) from the walk's
+// cell, -2 at the matrix border, -1 in a tile that was not computed.  The
+// look-ahead (< BT) crosses at most one tile edge per direction.
+template <typename Word, int R>
+__device__ __forceinline__ int nibble_back(const TileTable<Word> &T, const Word *const *tiles, const WalkPos &P,
+                                           int i, int j, int di, int dj, int p) {
+    const int ci = i - di * p, cj = j - dj * p;
+    if (ci <= 0 || cj <= 0) return -2;
+    int I = P.I, J = P.J, li = P.li - di * p, lj = P.lj - dj * p;
+    if (li < 0) { li += T.BT; --I; }
+    if (lj < 0) { lj += T.BT; --J; }
+    I -= T.I0;
+    J -= T.J0;
+    if (I < 0 || J < 0 || I >= T.nI || J >= T.nJ) return -1;
+    const Word *b = tiles[I * T.nJ + J];
     if (!b) return -1;
-    const int li = (i - 1) % T.BT, lj = (j - 1) % T.BT;
-    const Word w = __ldcg(b + (size_t)(li / T.R) * (size_t)T.BT + lj);
-    return (int)((unsigned long long)w >> (4 * (li % T.R))) & 15;
+    const Word w = __ldcg(b + (size_t)(li / R) * (size_t)T.BT + lj);
+    return (int)((unsigned long long)w >> (4 * (li % R))) & 15;
 }
 
-template <typename Word>
+template <typename Word, int R>
 __global__ void walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs, long long max_iters)
 {
+    __shared__ const Word *s_tiles[kWalkTableMax];
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
+    const int ntab = T.nI * T.nJ;
+    if (ntab > kWalkTableMax) {                          // the host keeps bands smaller than this
+        if (lane == 0) st->done = 2;
+        return;
+    }
+    for (int k = lane; k < ntab; k += 32) s_tiles[k] = T.bits[k];
+    __syncwarp();
     WalkState w = *st;
     auto emit = [&](int op, int cnt) {          // lane 0 only
         if (op == w.cur_op) { w.cur_len += cnt; return; }
@@ -74,63 +95,61 @@ __global__ void walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs, 
     };
     long long it = 0;
     while (w.done == 0 && ++it < max_iters) {
+        if (w.state == 0 && (w.i == 0 || w.j == 0)) { w.done = 1; break; }
+        // the next 32 * kLook cells of the run: the diagonal in state H, the row to the
+        // left in state E, the column above in state F; all loads are issued at once
+        const int di = w.state == 1 ? 0 : 1, dj = w.state == 2 ? 0 : 1;
+        const int mask = w.state == 0 ? 3 : (w.state == 1 ? 4 : 8);
+        WalkPos P;
+        P.I = (max(w.i, 1) - 1) / T.BT;
+        P.J = (max(w.j, 1) - 1) / T.BT;
+        P.li = (w.i - 1) - P.I * T.BT;
+        P.lj = (w.j - 1) - P.J * T.BT;
+        int nb[kLook];
+#pragma unroll
+        for (int q = 0; q < kLook; ++q)
+            nb[q] = nibble_back<Word, R>(T, s_tiles, P, w.i, w.j, di, dj, q * 32 + lane);
+        // first cell that ends the run: in H a source other than "diagonal", in E / F
+        // the opened bit; a missing tile or the border ends it too
+        int pos = 32 * kLook, nbk = 0;
+#pragma unroll
+        for (int q = 0; q < kLook; ++q) {
+            const bool end = nb[q] < 0 || (w.state == 0 ? (nb[q] & 3) != 1 : (nb[q] & mask) != 0);
+            const unsigned ends = __ballot_sync(kFull, end);
+            if (ends) {
+                const int k = __ffs(ends) - 1;
+                pos = q * 32 + k;
+                nbk = __shfl_sync(kFull, nb[q], k);
+                break;
+            }
+        }
+        const int op = w.state;                          // M, I or D runs of states H, E, F
+        if (pos == 32 * kLook) {                         // the whole look-ahead continues the run
+            if (lane == 0) emit(op, pos);
+            w.i -= di * pos;
+            w.j -= dj * pos;
+            continue;
+        }
         if (w.state == 0) {
-            if (w.i == 0 || w.j == 0) { w.done = 1; break; }
-            // lanes look at the diagonal (i - l, j - l)
-            const int ci = w.i - lane, cj = w.j - lane;
-            const int nb = (ci > 0 && cj > 0) ? nibble_at(T, ci, cj) : -2;   // -2: border
-            const unsigned notdiag = __ballot_sync(kFull, nb < 0 || (nb & 3) != 1);
-            const int k = notdiag ? __ffs(notdiag) - 1 : 32;   // leading diagonal cells
-            const int nbk = __shfl_sync(kFull, nb, k & 31);
-            if (lane == 0 && k > 0) emit(0, k);
-            w.i -= k;
-            w.j -= k;
-            if (k == 32) continue;
-            if (nbk == -2) { w.done = 1; break; }              // reached the border
-            if (nbk == -1) break;                              // tile not computed: ask the host
+            if (lane == 0 && pos > 0) emit(0, pos);
+            w.i -= pos;
+            w.j -= pos;
+            if (nbk == -2) { w.done = 1; break; }        // reached the border
+            if (nbk == -1) break;                        // tile not computed: ask the host
             const int src = nbk & 3;
             if (src == 0) { w.done = 1; break; }
             w.state = (src == 2) ? 1 : 2;
-        } else if (w.state == 1) {
-            // lanes look left along the row: cells (i, j - l)
-            const int cj = w.j - lane;
-            const int nb = cj > 0 ? nibble_at(T, w.i, cj) : -2;
-            const unsigned stop = __ballot_sync(kFull, nb < 0 || (nb & 4));
-            const int k = stop ? __ffs(stop) - 1 : 32;          // cells that extend the gap
-            const int nbk = __shfl_sync(kFull, nb, k & 31);
-            if (k == 32) {
-                if (lane == 0) emit(1, 32);
-                w.j -= 32;
-                continue;
-            }
-            if (nbk == -1) {                                   // missing tile: consume what was read
-                if (lane == 0 && k > 0) emit(1, k);
-                w.j -= k;
-                break;
-            }
-            if (nbk == -2) { w.done = 2; break; }              // a gap cannot reach column 0
-            if (lane == 0) emit(1, k + 1);                     // k extensions and the opening cell
-            w.j -= k + 1;
-            w.state = 0;
         } else {
-            const int ci = w.i - lane;
-            const int nb = ci > 0 ? nibble_at(T, ci, w.j) : -2;
-            const unsigned stop = __ballot_sync(kFull, nb < 0 || (nb & 8));
-            const int k = stop ? __ffs(stop) - 1 : 32;
-            const int nbk = __shfl_sync(kFull, nb, k & 31);
-            if (k == 32) {
-                if (lane == 0) emit(2, 32);
-                w.i -= 32;
-                continue;
-            }
-            if (nbk == -1) {
-                if (lane == 0 && k > 0) emit(2, k);
-                w.i -= k;
+            if (nbk == -1) {                             // missing tile: consume what was read
+                if (lane == 0 && pos > 0) emit(op, pos);
+                w.i -= di * pos;
+                w.j -= dj * pos;
                 break;
             }
-            if (nbk == -2) { w.done = 2; break; }
-            if (lane == 0) emit(2, k + 1);
-            w.i -= k + 1;
+            if (nbk == -2) { w.done = 2; break; }        // a gap cannot reach the border
+            if (lane == 0) emit(op, pos + 1);            // the extensions and the opening cell
+            w.i -= di * (pos + 1);
+            w.j -= dj * (pos + 1);
             w.state = 0;
         }
     }
