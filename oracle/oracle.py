@@ -90,6 +90,8 @@ class OracleLib:
                            ctypes.c_int, ctypes.c_int, i64p, i64p, i64p, i64p, i64p,
                            ctypes.c_char_p, i64p]
         lib.oracle_encode.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64, u8p, i64p]
+        lib.oracle_nw_score.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, u8p,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
         self.lib = lib
 
     def sw_score(self, a, b, S, gap_open: int, gap_extend: int):
@@ -102,6 +104,16 @@ class OracleLib:
         if rc != 0:
             raise ValueError("oracle_sw_score failed with %d" % rc)
         return sc.value, ae.value, be.value
+
+    def nw_score(self, a, b, S, gap_open: int, gap_extend: int) -> int:
+        """Global (end-to-end) Gotoh score of a against b."""
+        a, b, S = _u8(a), _u8(b), _mat(S)
+        sc = ctypes.c_int64()
+        rc = self.lib.oracle_nw_score(_ptr(a), a.size, _ptr(b), b.size, S.ctypes.data, S.shape[0],
+                                      int(gap_open), int(gap_extend), ctypes.byref(sc))
+        if rc != 0:
+            raise ValueError("oracle_nw_score failed (%d)" % rc)
+        return sc.value
 
     def _align(self, fn, a, b, S, gap_open, gap_extend) -> Alignment:
         a, b, S = _u8(a), _u8(b), _mat(S)
@@ -158,6 +170,11 @@ def sw_align(a, b, S, gap_open: int, gap_extend: int) -> Alignment:
 def sw_align_ptr(a, b, S, gap_open: int, gap_extend: int) -> Alignment:
     """Canonical alignment from traceback pointers."""
     return _get().sw_align_ptr(a, b, S, gap_open, gap_extend)
+
+
+def nw_score(a, b, S, gap_open: int, gap_extend: int) -> int:
+    """Global (end-to-end) Gotoh score: checks pieces of long local alignments."""
+    return _get().nw_score(a, b, S, gap_open, gap_extend)
 
 
 def encode(alphabet: str, text: str) -> np.ndarray:

@@ -71,6 +71,51 @@ static int better_end(int64_t h, int64_t i, int64_t j,
 }
 
 /*
+ * Global (end-to-end) Gotoh score of a against b: the best alignment that
+ * consumes all of a and all of b, with the same gap cost o + (k-1)e and no
+ * zero floor.  It is used to check pieces of a local alignment: a piece of
+ * an optimal path that starts and ends next to M columns is itself an
+ * optimal global alignment of the sub-block it spans (otherwise splicing the
+ * better one in would improve the whole path).
+ *   H(0,0) = 0; H(i,0) = -(o + (i-1)e) and H(0,j) = -(o + (j-1)e) for i, j >= 1
+ *   E(i,j) = max(E(i,j-1) - e, H(i,j-1) - o), F likewise down the column,
+ *   H(i,j) = max(H(i-1,j-1) + S(a_i,b_j), E(i,j), F(i,j)); the score is H(m,n).
+ */
+int oracle_nw_score(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                    const int8_t *S, int K, int o, int e, int64_t *score)
+{
+    if (!args_ok(a, m, b, n, S, K, o, e) || !score) return -1;
+    int64_t *Hrow = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *Frow = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!Hrow || !Frow) { free(Hrow); free(Frow); return -2; }
+    Hrow[0] = 0;
+    Frow[0] = ORACLE_NEG_INF;
+    for (int64_t j = 1; j <= n; j++) { Hrow[j] = -(o + (j - 1) * (int64_t)e); Frow[j] = ORACLE_NEG_INF; }
+    for (int64_t i = 1; i <= m; i++) {
+        int64_t E = ORACLE_NEG_INF;                      /* E(i,0) */
+        int64_t Hleft = -(o + (i - 1) * (int64_t)e);     /* H(i,0) */
+        int64_t Hdiag = Hrow[0];                          /* H(i-1,0) */
+        for (int64_t j = 1; j <= n; j++) {
+            int64_t Hup = Hrow[j];
+            E = max2(E - e, Hleft - o);
+            int64_t F = max2(Frow[j] - e, Hup - o);
+            int64_t H = Hdiag + S[a[i - 1] * K + b[j - 1]];
+            H = max2(H, E);
+            H = max2(H, F);
+            Frow[j] = F;
+            Hdiag = Hup;
+            Hrow[j] = H;
+            Hleft = H;
+        }
+        Hrow[0] = -(o + (i - 1) * (int64_t)e);
+    }
+    *score = Hrow[n];
+    if (m == 0) *score = n == 0 ? 0 : -(o + (n - 1) * (int64_t)e);
+    free(Hrow); free(Frow);
+    return 0;
+}
+
+/*
  * Score and canonical end cell, linear memory.  One row of H and F is kept;
  * the loops visit every cell of the (m+1) x (n+1) table once.
  */

@@ -29,6 +29,26 @@ def enumerate_alignments(a, b, S, go, ge):
                     stack.append((i + 1, j, "D", sc - (ge if last == "D" else go), ops + "D"))
 
 
+def brute_force_global(a, b, S, go, ge):
+    """Best score over every global alignment (all of a against all of b),
+    listed one by one and scored from the definition, for tiny sequences."""
+    m, n = len(a), len(b)
+    best = None
+    stack = [(0, 0, "", 0)]
+    while stack:
+        i, j, last, sc = stack.pop()
+        if i == m and j == n:
+            best = sc if best is None else max(best, sc)
+            continue
+        if i < m and j < n:
+            stack.append((i + 1, j + 1, "M", sc + int(S[a[i]][b[j]])))
+        if j < n:
+            stack.append((i, j + 1, "I", sc - (ge if last == "I" else go)))
+        if i < m:
+            stack.append((i + 1, j, "D", sc - (ge if last == "D" else go)))
+    return best
+
+
 def backward_moves(ops: str):
     """Rank sequence of the backward walk that reproduces ``ops``.
 

@@ -16,11 +16,13 @@ from oracle import oracle as O
 
 # (name, original text, planted mistake); each original must occur exactly once.
 MUTANTS = [
-    ("extend uses open (score)", "E = max2(E - e, Hleft - o);", "E = max2(E - o, Hleft - o);"),
-    ("F sign error (score)", "int64_t F = max2(Frow[j] - e, Hup - o);",
-     "int64_t F = max2(Frow[j] + e, Hup - o);"),
-    ("transposed matrix (score)", "int64_t H = Hdiag + S[a[i - 1] * K + b[j - 1]];",
-     "int64_t H = Hdiag + S[b[j - 1] * K + a[i - 1]];"),
+    ("extend uses open (score)", "E = max2(E - e, Hleft - o);                 /* E(i,j) */",
+     "E = max2(E - o, Hleft - o);                 /* E(i,j) */"),
+    ("F sign error (score)", "int64_t F = max2(Frow[j] - e, Hup - o);     /* F(i,j) */",
+     "int64_t F = max2(Frow[j] + e, Hup - o);     /* F(i,j) */"),
+    ("transposed matrix (score)",
+     "int64_t H = Hdiag + S[a[i - 1] * K + b[j - 1]];\n            H = max2(H, E);\n            H = max2(H, F);\n            H = max2(H, 0);",
+     "int64_t H = Hdiag + S[b[j - 1] * K + a[i - 1]];\n            H = max2(H, E);\n            H = max2(H, F);\n            H = max2(H, 0);"),
     ("dropped zero floor (score)", "            H = max2(H, 0);\n            Frow[j] = F;",
      "            Frow[j] = F;"),
     ("column-major end tie-break", "    if (i != bi) return i < bi;\n    return j < bj;",
@@ -37,6 +39,10 @@ MUTANTS = [
     ("extend before open (ptr)", "if (Fcur == f_open) p |= 8;", "if (Fcur == f_ext) p |= 8;"),
     ("E source mislabelled (ptr)", "else if (h == Ecur) src = 2;", "else if (h == Fcur) src = 2;"),
     ("no stop at zero (full)", "                if (h == 0) break;\n", "                if (i == 0 || j == 0) break;\n"),
+    ("leading gap priced per letter (global)", "        Hrow[0] = -(o + (i - 1) * (int64_t)e);",
+     "        Hrow[0] = -(i * (int64_t)e);"),
+    ("zero floor in the global score", "            H = max2(H, F);\n            Frow[j] = F;\n            Hdiag = Hup;\n            Hrow[j] = H;\n            Hleft = H;\n        }\n        Hrow[0]",
+     "            H = max2(H, F);\n            H = max2(H, 0);\n            Frow[j] = F;\n            Hdiag = Hup;\n            Hrow[j] = H;\n            Hleft = H;\n        }\n        Hrow[0]"),
 ]
 
 
@@ -52,6 +58,8 @@ def _battery(lib):
         ("kadane", lambda: pins.test_huge_gaps_is_kadane(lib)),
         ("self-dna", lambda: pins.test_self_alignment_dna_closed_form(lib)),
         ("rescoring", lambda: pins.test_rescoring_medium_cases(lib)),
+        ("global-bruteforce", lambda: pins.test_global_score_bruteforce(lib)),
+        ("global-closed", lambda: pins.test_global_score_closed_forms(lib)),
     ]
     for name, fn in checks:
         try:

@@ -223,3 +223,35 @@ def test_encode(oracle_mod):
     assert list(codes) == list(range(24))
     with pytest.raises(ValueError):
         oracle_mod.encode("ACGT", "ACGN")
+
+
+def test_global_score_bruteforce(oracle_mod):
+    """The global Gotoh score equals the best of all enumerated global
+    alignments (leading and trailing gaps included), for random tiny pairs,
+    2- and 4-letter alphabets and several gap costs, empty sides included."""
+    from bruteforce import brute_force_global
+    rng = np.random.default_rng(W.BASE_SEED + 7100)
+    for _ in range(120):
+        K = int(rng.choice([2, 4]))
+        S = rng.integers(-4, 5, size=(K, K)).astype(np.int8)
+        S = np.triu(S) + np.triu(S, 1).T
+        go = int(rng.integers(0, 7))
+        ge = int(rng.integers(0, go + 1))
+        a = rng.integers(0, K, size=int(rng.integers(0, 6))).astype(np.uint8)
+        b = rng.integers(0, K, size=int(rng.integers(0, 6))).astype(np.uint8)
+        assert oracle_mod.nw_score(a, b, S, go, ge) == brute_force_global(list(a), list(b), S, go, ge), \
+            (list(a), list(b), S.tolist(), go, ge)
+
+
+def test_global_score_closed_forms(oracle_mod):
+    """Identical DNA aligns end to end with no gap; one side empty costs one gap."""
+    S = W.dna_matrix()
+    a = W.uniform_dna(300, W.BASE_SEED + 7200)
+    assert oracle_mod.nw_score(a, a, S, 5, 2) == 300
+    assert oracle_mod.nw_score(a[:7], a[:0], S, 5, 2) == -(5 + 6 * 2)
+    assert oracle_mod.nw_score(a[:0], a[:0], S, 5, 2) == 0
+    # a local alignment that spans both sequences end to end scores the global optimum
+    b = W.mutate(a, 4, W.BASE_SEED + 7201, p_sub=0.02, p_indel=0.0)
+    loc = oracle_mod.sw_align(a, b, S, 5, 2)
+    if (loc.a_begin, loc.b_begin, loc.a_end, loc.b_end) == (0, 0, len(a), len(b)):
+        assert oracle_mod.nw_score(a, b, S, 5, 2) == loc.score
