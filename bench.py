@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--workloads", default="all",
                     help="comma list of the other workloads to measure after the headline: "
-                         "dna2k,dbsearch,batch,serve (default all; 'none' for the headline only)")
+                         "dna2k,dbsearch,batch,serve,dna5m (default all; 'none' for the headline only)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate (500 = full)")
     ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000")
     return ap.parse_args()
@@ -339,7 +339,7 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(args)
         wl = [] if args.workloads == "none" else (
-            ["dna2k", "dbsearch", "batch", "serve"] if args.workloads == "all" else args.workloads.split(","))
+            ["dna2k", "dbsearch", "batch", "serve", "dna5m"] if args.workloads == "all" else args.workloads.split(","))
         if wl and args.mode == "align":
             from paper_2211_10769_gb300 import bench_workloads as BW
             out["workloads"] = BW.run_all(wl, args)

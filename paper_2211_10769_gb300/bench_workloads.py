@@ -11,7 +11,8 @@ CUDA events on the context's stream and returns a small dict:
               uneven pairs versus one sw_score call per pair;
 * serve    -- the continuous-batching server under Poisson arrivals at each
               rate: p50 / p99 latency (arrival to result on the host),
-              sustained GCUPS, admitted / deferred submissions.
+              sustained GCUPS, admitted / deferred submissions;
+* dna5m    -- sw_align of the 5 Mbp x 5 Mbp variant of the long DNA pair.
 """
 from __future__ import annotations
 
@@ -68,20 +69,29 @@ def dbsearch(ctx, torch, stream, args):
     qs, pdb = _protein_db()
     db = Database(ctx, pdb.residues, pdb.offsets)
     total_res = int(pdb.residues.size)
+    from .binding import KT_DB16
     per_query = []
+    kern_s = 0.0
     for q in qs:
         db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20)
+        ctx.timing(True)
         ts = _timed(torch, stream, lambda: db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20), 3)
+        kms, kn = ctx.kernel_time(KT_DB16)
+        ctx.timing(False)
         t = statistics.median(ts)
-        per_query.append({"m": len(q), "ms": round(1e3 * t, 2), "gcups": round(len(q) * total_res / t / 1e9, 1)})
+        kern_s += kms / 1e3 / max(1, kn)
+        per_query.append({"m": len(q), "ms": round(1e3 * t, 2), "gcups": round(len(q) * total_res / t / 1e9, 1),
+                          "fill_ms": round(kms / max(1, kn), 2)})
     cells = sum(len(q) for q in qs) * total_res
     t_all = sum(x["ms"] for x in per_query) / 1e3
     peak16 = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6       # two 16-bit lanes per 32-bit lane
     db.close()
+    # the packed fill reads every subject residue once per query sweep (1 B per residue)
     return {"workload": "protein_dbsearch_5q_x_500k", "nseq": pdb.nseq, "residues": total_res,
             "cells": cells, "seconds": round(t_all, 3), "gcups": round(cells / t_all / 1e9, 1),
             "per_query": per_query,
-            "alu_frac_16bit_lanes": round(OPS_PER_CELL * cells / t_all / peak16, 4)}
+            "alu_frac_16bit_lanes": round(OPS_PER_CELL * cells / t_all / peak16, 4),
+            "fill_hbm_gbs": round(len(qs) * total_res / kern_s / 1e9, 1)}
 
 
 def batch(ctx, torch, stream, args):
@@ -176,6 +186,26 @@ def serve(ctx, torch, stream, args):
             "rates": out}
 
 
+def dna5m(ctx, torch, stream, args):
+    """The 5 Mbp x 5 Mbp variant of the long pair: one warm-up and one timed sw_align."""
+    from .binding import KT_FILL, KT_FILL_TB, KT_WALK
+    sc = W.dna_scoring()
+    A, B = W.dna_long_pair(5_000_000)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    ref = ctx.align(dA, dB, sc.matrix, sc.gap_open, sc.gap_extend)
+    ctx.timing(True)
+    ts = _timed(torch, stream, lambda: ctx.align(dA, dB, sc.matrix, sc.gap_open, sc.gap_extend), 1)
+    k = {nm: ctx.kernel_time(kind) for nm, kind in (("fill", KT_FILL), ("fill_tb", KT_FILL_TB), ("walk", KT_WALK))}
+    ctx.timing(False)
+    t = ts[0]
+    cells = len(A) * len(B)
+    return {"workload": "dna_pair_5mbp_align", "m": len(A), "n": len(B), "cells": cells,
+            "seconds": round(t, 3), "gcups": round(cells / t / 1e9, 1),
+            "kernel_s": {nm: round(v[0] / 1e3, 3) for nm, v in k.items()},
+            "result": {"score": ref.score, "a": [ref.a_begin, ref.a_end], "b": [ref.b_begin, ref.b_end],
+                       "cigar_len": len(ref.cigar)}}
+
+
 def run_all(names, args):
     import torch
     from .binding import Context
@@ -183,7 +213,7 @@ def run_all(names, args):
     ctx = Context(0, stream)
     res = {}
     for nm in names:
-        fn = {"dna2k": dna2k, "dbsearch": dbsearch, "batch": batch, "serve": serve}[nm]
+        fn = {"dna2k": dna2k, "dbsearch": dbsearch, "batch": batch, "serve": serve, "dna5m": dna5m}[nm]
         t0 = time.perf_counter()
         try:
             res[nm] = fn(ctx, torch, stream, args)

@@ -385,8 +385,14 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
     if (const char *f = std::getenv("SWGB_TB_SW")) c->tb_strip_warps = std::atoi(f);
-    c->ckpt_budget = (size_t)4 << 30;
+    // checkpoint memory of sw_align: 40% of the device memory free now (at least 4 GB), so that
+    // the tiles stay small on long pairs (5 Mbp x 5 Mbp needs about 100 GB for 4096-cell tiles);
+    // traceback bits of one band: 4 GB
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    c->ckpt_budget = std::max<size_t>((size_t)4 << 30, (size_t)((double)free_b * 0.4));
     c->tb_budget = (size_t)4 << 30;
+    if (const char *f = std::getenv("SWGB_CKPT_BUDGET_MB")) c->ckpt_budget = (size_t)std::atoll(f) << 20;
     *out = c;
     return SW_OK;
 }

@@ -159,8 +159,11 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->walk.ensure(sizeof(WalkState)));
     RC(c->runs.ensure((size_t)(ie + je + 2) * sizeof(int2)));
     WalkState w{ie, je, 0, 0, 0, -1, 0};
-    // a band of three tiles per tile row, deep enough for about one tile per SM
-    const int band = c->tb_band > 0 ? std::min(c->tb_band, 60) : std::max(kMinBandDepth, c->nsm / 3);
+    // a band of three tiles per tile row, deep enough for about one tile per SM, and its
+    // traceback bits within the budget
+    const size_t tile_bytes = (size_t)(BT / tbc.R) * (size_t)BT * (size_t)tb_word_bytes(tbc.R);
+    int band = c->tb_band > 0 ? std::min(c->tb_band, 60) : std::max(kMinBandDepth, c->nsm / 3);
+    band = (int)std::max<long long>(1, std::min<long long>(band, (long long)(c->tb_budget / (3 * tile_bytes))));
     const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
     const int HS = tsw * 32 * tbc.R;                     // rows per traceback strip
     const size_t table_cap = (size_t)(band + 1) * (band + 2);
@@ -171,8 +174,6 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
 
     // ---- 3. rounds: recompute a band of tiles, walk through it
     const int R = tbc.R;
-    const size_t tile_words = (size_t)(BT / R) * (size_t)BT;
-    const size_t tile_bytes = tile_words * (size_t)tb_word_bytes(R);
     const int maxtiles = 3 * band;
     RC(c->tb.ensure(tile_bytes * maxtiles));
     RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));

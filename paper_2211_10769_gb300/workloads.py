@@ -136,18 +136,23 @@ def mutate(seq: np.ndarray, alphabet_size: int, seed: int, p_sub: float = 0.10,
     kind = g.random(n) < 0.5
     lens = g.geometric(1.0 / mean_indel, size=n)
     pieces = []
+    evpos = np.flatnonzero(ev)
+    e = 0
     k = 0
     while k < n:
-        if ev[k]:
-            if kind[k]:  # insertion before base k
-                pieces.append(g.integers(0, alphabet_size, size=int(lens[k]), dtype=np.uint8))
-                pieces.append(out_base[k:k + 1])
-                k += 1
-            else:        # deletion of lens[k] bases starting at k
-                k += int(lens[k])
-        else:
+        while e < len(evpos) and evpos[e] < k:     # events inside a deletion are skipped
+            e += 1
+        nxt = int(evpos[e]) if e < len(evpos) else n
+        if nxt > k:                                  # bases up to the next event are kept
+            pieces.append(out_base[k:nxt])
+            k = nxt
+            continue
+        if kind[k]:  # insertion before base k
+            pieces.append(g.integers(0, alphabet_size, size=int(lens[k]), dtype=np.uint8))
             pieces.append(out_base[k:k + 1])
             k += 1
+        else:        # deletion of lens[k] bases starting at k
+            k += int(lens[k])
     return np.concatenate(pieces) if pieces else np.zeros(0, dtype=np.uint8)
 
 

@@ -267,3 +267,32 @@ def test_kernel_timing(ctx):
     assert ctx.kernel_time(binding.KT_FILL) == (0.0, 0)
     with pytest.raises(binding.SwError):
         ctx.kernel_time(7)
+
+
+def test_bounded_wait_timeout(oracle_mod, monkeypatch):
+    """Failure detection without a GPU fault: with a spin limit of one poll
+    every cross-warp wait of the fill gives up at once, the kernel records
+    the timeout in its error word and returns; the call reports SW_ETIMEOUT
+    and the process and device stay usable."""
+    from paper_2211_10769_gb300 import binding, build
+    build.build()
+    sc = W.dna_scoring()
+    a = W.uniform_dna(20_000, W.BASE_SEED + 9900)
+    b = W.mutate(a, 4, W.BASE_SEED + 9901, p_sub=0.1, p_indel=0.02)
+    monkeypatch.setenv("SWGB_SPIN_LIMIT", "1")
+    c = binding.Context(0)
+    try:
+        for call in (c.score, c.align):
+            with pytest.raises(binding.SwError) as ei:
+                call(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+            assert ei.value.status == binding.SW_ETIMEOUT
+    finally:
+        c.close()
+    monkeypatch.delenv("SWGB_SPIN_LIMIT")
+    c2 = binding.Context(0)
+    try:
+        want = oracle_mod.sw_score(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+        got = c2.score(a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+        assert (got.score, got.a_end, got.b_end) == want
+    finally:
+        c2.close()
