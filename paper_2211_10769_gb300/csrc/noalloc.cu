@@ -65,7 +65,7 @@ int setup_device(int dev, unsigned char **out) {
             cudaGetLastError();
             return SW_ECUDA;
         }
-        if (cudaFuncSetAttribute(wavefront_kernel<kR, kW, kModeScore, false>,
+        if (cudaFuncSetAttribute(wavefront_kernel<kR, kW, kModeScore, kProf8>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (kMaxAlphabet + 1) * kHC) != cudaSuccess) {
             cudaGetLastError();
@@ -136,10 +136,10 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     L.err = err; L.total = nstrips; L.spin_limit = 1LL << 26; L.ntasks = 1;
     const size_t smem = (size_t)(ds.K + 1) * kHC;
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wavefront_kernel<kR, kW, kModeScore, false>, (kW + 2) * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wavefront_kernel<kR, kW, kModeScore, kProf8>, (kW + 2) * 32, smem));
     if (occ < 1) return SW_ECUDA;
     const long long grid = std::min<long long>(nstrips, (long long)occ * nsm);
-    wavefront_kernel<kR, kW, kModeScore, false><<<(unsigned)grid, (kW + 2) * 32, smem, st>>>(L);
+    wavefront_kernel<kR, kW, kModeScore, kProf8><<<(unsigned)grid, (kW + 2) * 32, smem, st>>>(L);
     CU(cudaGetLastError());
     reduce_candidates_kernel<<<1, 32, 0, st>>>(task, 1, cand, result);
     CU(cudaGetLastError());

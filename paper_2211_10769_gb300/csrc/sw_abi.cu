@@ -125,15 +125,19 @@ int swgb::map_kernel_error(int e) {
 
 namespace {
 
-template <int R, int W, int MODE, bool FOLD>
+// shared memory of an int32 query profile, at most (so that two blocks still fit an SM)
+constexpr size_t kProf32MaxBytes = 64 * 1024;
+
+template <int R, int W, int MODE, int PK>
 int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int max_blocks) {
-    auto kern = wavefront_kernel<R, W, MODE, FOLD>;
+    auto kern = wavefront_kernel<R, W, MODE, PK>;
     constexpr int HC = W * 32 * R;
-    const size_t smem = (size_t)(K + 1) * HC;
+    constexpr size_t PB = PK == kProf32 ? 4 : 1;
+    const size_t smem = (size_t)(K + 1) * HC * PB;
     static int attr_set[64] = {0};
     if (c->device < 64 && !attr_set[c->device]) {
-        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)((kMaxAlphabet + 1) * HC)));
+        const size_t cap = PK == kProf32 ? kProf32MaxBytes : (size_t)(kMaxAlphabet + 1) * HC;
+        CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
         attr_set[c->device] = 1;
     }
     int occ = 0;
@@ -149,15 +153,24 @@ int launch_fill_cfg(sw_ctx *c, const FillLaunch &L, int K, long long tickets, in
     return SW_OK;
 }
 
+template <int R, int W, int MODE>
+int launch_fill_pk(sw_ctx *c, int pk, const FillLaunch &L, int K, long long tickets, int B) {
+    switch (pk) {
+        case kProf8: return launch_fill_cfg<R, W, MODE, kProf8>(c, L, K, tickets, B);
+        case kProf8Fold: return launch_fill_cfg<R, W, MODE, kProf8Fold>(c, L, K, tickets, B);
+        default: return launch_fill_cfg<R, W, MODE, kProf32>(c, L, K, tickets, B);
+    }
+}
+
 template <int R, int W>
 int launch_fill_rw(sw_ctx *c, int mode, bool fold, const FillLaunch &L, int K, long long tickets, int B) {
-    switch (mode * 2 + (fold ? 1 : 0)) {
-        case 0: return launch_fill_cfg<R, W, kModeScore, false>(c, L, K, tickets, B);
-        case 1: return launch_fill_cfg<R, W, kModeScore, true>(c, L, K, tickets, B);
-        case 2: return launch_fill_cfg<R, W, kModeScoreCk, false>(c, L, K, tickets, B);
-        case 3: return launch_fill_cfg<R, W, kModeScoreCk, true>(c, L, K, tickets, B);
-        case 4: return launch_fill_cfg<R, W, kModeTb, false>(c, L, K, tickets, B);
-        case 5: return launch_fill_cfg<R, W, kModeTb, true>(c, L, K, tickets, B);
+    // int32 profile when it is small (DNA-like alphabets), else int8 (+ open when it fits)
+    const bool p32 = c->prof32 && (size_t)(K + 1) * (size_t)(W * 32 * R) * 4 <= kProf32MaxBytes;
+    const int pk = p32 ? kProf32 : (fold ? kProf8Fold : kProf8);
+    switch (mode) {
+        case kModeScore: return launch_fill_pk<R, W, kModeScore>(c, pk, L, K, tickets, B);
+        case kModeScoreCk: return launch_fill_pk<R, W, kModeScoreCk>(c, pk, L, K, tickets, B);
+        case kModeTb: return launch_fill_pk<R, W, kModeTb>(c, pk, L, K, tickets, B);
         default: return SW_EINVAL;
     }
 }
@@ -383,6 +396,7 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     }
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
+    if (const char *f = std::getenv("SWGB_PROF32")) c->prof32 = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
     if (const char *f = std::getenv("SWGB_TB_SW")) c->tb_strip_warps = std::atoi(f);
     // checkpoint memory of sw_align: 40% of the device memory free now (at least 4 GB), so that

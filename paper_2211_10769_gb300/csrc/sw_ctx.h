@@ -71,6 +71,7 @@ struct sw_ctx {
     bool fwd_auto = true;             // choose R per pair (pair_fill_config)
     swgb::FillConfig tbc{8, 4};       // traceback recompute
     swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
+    bool prof32 = true;               // int32 query profiles where they fit (small alphabets)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
     int tb_strip_warps = 0;           // compute warps per traceback strip (0 = all)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align

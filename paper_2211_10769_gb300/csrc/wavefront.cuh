@@ -31,8 +31,9 @@
 // because H = max(X, F) and F - o <= F - e; so the dependency from one row
 // to the next is a single max-add, and H = max(X, F), H - o = max(F - o,
 // X - o) follow off that chain.  Scores come from a per-strip query profile
-// in shared memory, prof[c*HC + r] = S(a_r, c) (int8, padding residue
-// c = K at -128), one vector load and one prmt per cell.
+// in shared memory, prof[c*HC + r] = S(a_r, c) (int8 with one prmt per
+// cell, or int32 for small alphabets; padding residue c = K at -128), one
+// vector load per step.
 //
 // Modes: score (TB = false) keeps, per lane, the best H with its first
 // row, then first column (a branch-free row key, see row_key), and writes
@@ -99,9 +100,28 @@ template <> struct TbWord<8> { using T = uint32_t; };
 template <> struct TbWord<12> { using T = unsigned long long; };
 template <> struct TbWord<16> { using T = unsigned long long; };
 
-template <int R>
-__device__ __forceinline__ void load_profile(const int8_t *p, uint32_t (&w)[R / 4]) {
-    if constexpr (R == 4) {
+// Query profile kinds: int8 scores S, int8 scores S + open ("folded", the
+// open penalty is then free in the cell update), or int32 scores S + open
+// (no byte extraction per cell; four times the shared memory, so only for
+// small alphabets).
+enum ProfKind { kProf8 = 0, kProf8Fold = 1, kProf32 = 2 };
+
+template <int R, int PK>
+struct ProfWords { static constexpr int N = PK == kProf32 ? R : R / 4; };   // 32-bit words per lane
+
+// int32 profiles are stored chunk-major so that every 16-byte load of a warp
+// is conflict-free: residue c, lane g (of the strip's NL = W*32 lanes), rows
+// 4q .. 4q+3 of the lane sit at int32 index ((c*(R/4) + q)*NL + g)*4.  A lane
+// passes p = its first chunk of residue c; chunk q is NL*16 bytes further on.
+template <int R, int PK, int NL = 0>
+__device__ __forceinline__ void load_profile(const int8_t *p, uint32_t (&w)[ProfWords<R, PK>::N]) {
+    if constexpr (PK == kProf32) {
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(p + (size_t)q * NL * 16);
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+    } else if constexpr (R == 4) {
         w[0] = *reinterpret_cast<const uint32_t *>(p);
     } else if constexpr (R == 8) {
         const uint2 v = *reinterpret_cast<const uint2 *>(p);
@@ -122,6 +142,12 @@ __device__ __forceinline__ int score_byte(const uint32_t *w, int r) {
         case 2: return sext8<2>(w[r >> 2]);
         default: return sext8<3>(w[r >> 2]);
     }
+}
+
+template <int PK>
+__device__ __forceinline__ int score_at(const uint32_t *w, int r) {
+    if constexpr (PK == kProf32) return (int)w[r];
+    else return score_byte(w, r);
 }
 
 __device__ __forceinline__ int lds_acquire(const int *p) {
@@ -186,8 +212,8 @@ __device__ __forceinline__ int row_key(int u, int r) { return u * kKeyRows + (R 
 // entered with uup / fup = H - open and F of the row above at this column;
 // st.udiag0 holds H - open of the row above at the previous column.  TB
 // collects the four decision bits of every cell into word.
-template <int R, bool FOLD, bool TB>
-__device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (&pw)[R / 4], int uup, int fup,
+template <int R, int PK, bool TB>
+__device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int uup, int fup,
                                               int go, int ge, typename TbWord<R>::T &word)
 {
     int udiag = st.udiag0;
@@ -196,8 +222,8 @@ __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (
     int fopen_ref = uup;                                   // H(i-1,j) - open
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        int sp = score_byte(pw, r);                        // S (+ open when folded)
-        if constexpr (!FOLD) sp += go;
+        int sp = score_at<PK>(pw, r);                      // S (+ open when folded)
+        if constexpr (PK == kProf8) sp += go;
         const int uold = st.U[r];                          // H(i,j-1) - open
         const int e = __viaddmax_s32(st.E[r], -ge, uold);
         const int x = __viaddmax_s32_relu(udiag, sp, e);   // max(H(i-1,j-1) + S, E, 0)
@@ -222,8 +248,8 @@ __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (
 // One wavefront step of one lane: column j = s - lane of its R rows.
 // CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
 // a sweep); the steady state skips those tests.
-template <int R, int MODE, bool FOLD, bool CHECK>
-__device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[R / 4], int2 top,
+template <int R, int MODE, int PK, bool CHECK>
+__device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int2 top,
                                           int s, int lane, int n, int go, int ge,
                                           int2 *ring_out, typename TbWord<R>::T *tbw)
 {
@@ -233,7 +259,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     if (lane == 0) { uup = top.x; fup = top.y; }
     if (CHECK && (j < 0 || j >= n)) return;
     typename TbWord<R>::T word = 0;
-    column_update<R, FOLD, MODE == kModeTb>(st, pw, uup, fup, go, ge, word);
+    column_update<R, PK, MODE == kModeTb>(st, pw, uup, fup, go, ge, word);
     if (lane == 31) ring_out[j & (kQS - 1)] = make_int2(st.ub, st.fb);
     if constexpr (MODE == kModeTb) {
         tbw[j] = word;
@@ -248,7 +274,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     }
 }
 
-template <int R, int W, int MODE, bool FOLD>
+template <int R, int W, int MODE, int PK>
 __global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 12 ? 128 : (W > 4 ? 96 : 104))
 wavefront_kernel(const FillLaunch L)
 {
@@ -256,7 +282,9 @@ wavefront_kernel(const FillLaunch L)
     constexpr int CH = kCH, QS = kQS, QB = kQB, IOB = kIOB;
     static_assert(QS >= 2 * IOB + 2 * CH + 64, "ring too small");
 
-    extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC
+    extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC scores of PB bytes
+    constexpr int PB = PK == kProf32 ? 4 : 1;
+    constexpr int NPW = ProfWords<R, PK>::N;
     __shared__ int2 ring[W + 1][QS];                 // channel k: producer k-1 (I/O for k=0), consumer k (I/O for k=W); (H - open, F)
     __shared__ uint8_t bring[QB];
     __shared__ int prod[W + 1];                      // columns available in channel k
@@ -304,9 +332,12 @@ wavefront_kernel(const FillLaunch L)
             const int r = rbase + lr;
             const bool ok = r < T.rows;
             const int av = ok ? min((int)T.a[r], K - 1) : 0;
-            for (int c = 0; c <= K; ++c)
-                prof[c * HC + lr] = (ok && c < K) ? (int8_t)(SC.mat[av * K + c] + (FOLD ? go : 0))
-                                                  : (int8_t)kPadScore;
+            for (int c = 0; c <= K; ++c) {
+                const int v = (ok && c < K) ? SC.mat[av * K + c] + (PK != kProf8 ? go : 0) : kPadScore;
+                if constexpr (PK == kProf32)
+                    reinterpret_cast<int32_t *>(prof)[((c * (R / 4) + (lr % R) / 4) * (W * 32) + lr / R) * 4 + (lr & 3)] = v;
+                else prof[c * HC + lr] = (int8_t)v;
+            }
         }
         __syncthreads();
 
@@ -395,7 +426,8 @@ wavefront_kernel(const FillLaunch L)
             // ================= compute warp =================
             const int lrow = (warp * 32 + lane) * R;        // first row of this lane within the strip
             const int grow = rbase + lrow;                  // ... within the task
-            const int8_t *prow = prof + lrow;
+            // this lane's first profile entry (int8: its R rows are contiguous; int32: chunk-major)
+            const int8_t *prow = PK == kProf32 ? prof + (warp * 32 + lane) * 16 : prof + lrow;
             LaneState<R> st;
 #pragma unroll
             for (int r = 0; r < R; ++r) { st.U[r] = -go; st.E[r] = kNeg; }
@@ -419,10 +451,10 @@ wavefront_kernel(const FillLaunch L)
                     const int fup = __shfl_up_sync(kFull, st.fb, 1);
                     if (k <= lane) {
                         const int cb = min((int)T.b[k - lane - 1], K);   // column c - lane + k
-                        uint32_t pwk[R / 4];
-                        load_profile<R>(prow + cb * HC, pwk);
+                        uint32_t pwk[NPW];
+                        load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
                         typename TbWord<R>::T unused = 0;
-                        column_update<R, FOLD, false>(st, pwk, uup, fup, go, ge, unused);
+                        column_update<R, PK, false>(st, pwk, uup, fup, go, ge, unused);
                     }
                 }
                 // the diagonal of the task's first column: the row above at column c
@@ -442,7 +474,7 @@ wavefront_kernel(const FillLaunch L)
             int seen_in = 0;
             bool loaded = false;             // inputs of step s0 were prefetched by the previous step
             int c;
-            uint32_t pw[R / 4];
+            uint32_t pw[NPW];
             int2 top;
             for (int s0 = 0; s0 < n + 31; s0 += CH) {
                 const int need_in = min(n, s0 + CH + 1);   // this chunk plus the next step's prefetch
@@ -456,7 +488,7 @@ wavefront_kernel(const FillLaunch L)
                     // inputs of the sweep's first step (later steps prefetch the next one)
                     const int j = s0 - lane;
                     c = ((unsigned)j < (unsigned)n) ? min((int)bring[j & (QB - 1)], K) : K;
-                    load_profile<R>(prow + c * HC, pw);
+                    load_profile<R, PK, W * 32>(prow + c * HC * PB, pw);
                     top = rin[s0 & (QS - 1)];
                     loaded = true;
                 }
@@ -467,11 +499,11 @@ wavefront_kernel(const FillLaunch L)
                         const int s = s0 + k;
                         const int cn = min((int)bring[(s + 1 - lane) & (QB - 1)], K);
                         const int2 topn = rin[(s + 1) & (QS - 1)];
-                        uint32_t pwn[R / 4];
-                        load_profile<R>(prow + cn * HC, pwn);
-                        lane_step<R, MODE, FOLD, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                        uint32_t pwn[NPW];
+                        load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
+                        lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
-                        for (int q = 0; q < R / 4; ++q) pw[q] = pwn[q];
+                        for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
                     }
                 } else {
@@ -483,11 +515,11 @@ wavefront_kernel(const FillLaunch L)
                         const int jn = s + 1 - lane;
                         const int cn = ((unsigned)jn < (unsigned)n) ? min((int)bring[jn & (QB - 1)], K) : K;
                         const int2 topn = rin[(s + 1) & (QS - 1)];   // stale when s + 1 >= n: lane 0 skips that column
-                        uint32_t pwn[R / 4];
-                        load_profile<R>(prow + cn * HC, pwn);
-                        lane_step<R, MODE, FOLD, true>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                        uint32_t pwn[NPW];
+                        load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
+                        lane_step<R, MODE, PK, true>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
-                        for (int q = 0; q < R / 4; ++q) pw[q] = pwn[q];
+                        for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
                     }
                 }
