@@ -114,7 +114,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         return (size_t)((m / bt) * n + (n / bt) * m) * sizeof(int2);
     };
     while (ck_bytes(BT) > c->ckpt_budget && BT < (1LL << 30)) BT *= 2;
-    if (BT % HC != 0 || BT % HT != 0 || BT > (1LL << 30)) return SW_EINVAL;
+    // checkpoint columns are stored at chunk ends: BT must be a multiple of the chunk
+    if (BT % HC != 0 || BT % HT != 0 || BT % kCH != 0 || BT > (1LL << 30)) return SW_EINVAL;
     const long long nrowck = std::max<long long>(1, m / BT), ncolck = std::max<long long>(1, n / BT);
 
     // ---- 1. forward fill with row and column checkpoints
