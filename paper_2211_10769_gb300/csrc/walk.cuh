@@ -10,8 +10,8 @@
 //   state E: emit I, go left; back to H if the E-opened bit is set;
 //   state F: emit D, go up; back to H if the F-opened bit is set.
 //
-// One warp walks.  Runs are taken 128 cells at a time (each lane issues
-// four loads at once, so their latencies overlap): in state H the lanes
+// One warp walks.  Runs are taken 64 cells at a time (each lane issues
+// two loads at once, so their latencies overlap): in state H the lanes
 // read the cells of the diagonal ahead and the walk jumps over the leading
 // cells whose source is "diagonal"; in state E (F) they read the cells to
 // the left (above) and the walk jumps to the first one whose opened bit is
@@ -44,7 +44,8 @@ struct TileTable {
     int32_t R;                 // rows per word
 };
 
-constexpr int kLook = 4;           // groups of 32 cells each lane reads ahead per iteration
+constexpr int kLook = 2;           // groups of 32 cells each lane reads ahead per iteration (2 measured
+                                   // best of 1..16: runs are short, wasted look-ahead costs issue time)
 constexpr int kWalkTableMax = 4096;   // tile-table entries cached in shared memory
 
 // Where the walk is: its cell's tile (absolute tile row / column) and the
@@ -55,22 +56,27 @@ struct WalkPos {
 
 // Decision nibble of the cell p steps back along (di, dj) from the walk's
 // cell, -2 at the matrix border, -1 in a tile that was not computed.  The
-// look-ahead (< BT) crosses at most one tile edge per direction.
+// look-ahead (< BT) crosses at most one tile edge per direction.  The load
+// is unconditional (a cell without bits reads the valid word `dummy`
+// instead), so the loads of all look-ahead cells can be in flight together.
 template <typename Word, int R>
 __device__ __forceinline__ int nibble_back(const TileTable<Word> &T, const Word *const *tiles, const WalkPos &P,
-                                           int i, int j, int di, int dj, int p) {
+                                           int i, int j, int di, int dj, int p, const Word *dummy) {
     const int ci = i - di * p, cj = j - dj * p;
-    if (ci <= 0 || cj <= 0) return -2;
     int I = P.I, J = P.J, li = P.li - di * p, lj = P.lj - dj * p;
     if (li < 0) { li += T.BT; --I; }
     if (lj < 0) { lj += T.BT; --J; }
     I -= T.I0;
     J -= T.J0;
-    if (I < 0 || J < 0 || I >= T.nI || J >= T.nJ) return -1;
-    const Word *b = tiles[I * T.nJ + J];
-    if (!b) return -1;
-    const Word w = __ldcg(b + (size_t)(li / R) * (size_t)T.BT + lj);
-    return (int)((unsigned long long)w >> (4 * (li % R))) & 15;
+    const bool border = ci <= 0 || cj <= 0;
+    const bool inside = !border && I >= 0 && J >= 0 && I < T.nI && J < T.nJ;
+    const Word *b = inside ? tiles[I * T.nJ + J] : nullptr;
+    const bool have = b != nullptr;
+    const int lr = have ? li : 0;
+    const Word *addr = have ? b + (size_t)(lr / R) * (size_t)T.BT + lj : dummy;
+    const Word w = __ldcg(addr);
+    const int nib = (int)((unsigned long long)w >> (4 * (lr % R))) & 15;
+    return border ? -2 : (have ? nib : -1);
 }
 
 template <typename Word, int R>
@@ -108,7 +114,8 @@ __global__ void walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs, 
         int nb[kLook];
 #pragma unroll
         for (int q = 0; q < kLook; ++q)
-            nb[q] = nibble_back<Word, R>(T, s_tiles, P, w.i, w.j, di, dj, q * 32 + lane);
+            nb[q] = nibble_back<Word, R>(T, s_tiles, P, w.i, w.j, di, dj, q * 32 + lane,
+                                         reinterpret_cast<const Word *>(st));
         // first cell that ends the run: in H a source other than "diagonal", in E / F
         // the opened bit; a missing tile or the border ends it too
         int pos = 32 * kLook, nbk = 0;
