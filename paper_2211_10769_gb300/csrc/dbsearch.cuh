@@ -48,7 +48,45 @@ struct DbView {
     const int32_t *pairs;      // pair p = subjects pairs[2p], pairs[2p+1] (-1 = none)
     int32_t npairs;
     int32_t maxlen;
+    // scratch slots: one per block that can be resident at a time (nslots = SMs x blocks per
+    // SM); block b < nslots uses slot b, a later block (an oversubscribed grid) takes a slot a
+    // finished block has released
+    unsigned *slot_pool;       // bit set = slot taken; slots < min(grid, nslots) and >= nslots preset
+    int32_t slot_words;
+    int32_t nslots;
+    long long spin_limit;      // bound of the wait for a free slot
+    int *err;                  // error word (kErr*)
 };
+
+// Presets the slot pool: the first wave's slots are taken, slots that do not exist too.
+static __global__ void init_slot_pool_kernel(unsigned *pool, int words, int nslots, int first_wave) {
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
+        const int lo = w * 32;
+        unsigned v = 0;
+        for (int b = 0; b < 32; ++b) if (lo + b >= nslots || lo + b < first_wave) v |= 1u << b;
+        pool[w] = v;
+    }
+}
+
+// Acquires a scratch slot for this block (thread 0); -1 after a bounded wait.
+__device__ __forceinline__ int db_acquire_slot(const DbView &D) {
+    if ((int)blockIdx.x < D.nslots) return (int)blockIdx.x;
+    for (long long t = 0; t < D.spin_limit; ++t) {
+        const int w = (int)((blockIdx.x + t) % D.slot_words);
+        const unsigned cur = *reinterpret_cast<volatile unsigned *>(D.slot_pool + w);
+        if (cur != 0xffffffffu) {
+            const int b = __ffs(~cur) - 1;
+            if (!(atomicOr(D.slot_pool + w, 1u << b) & (1u << b))) {
+                __threadfence();                  // after the previous holder's release
+                return w * 32 + b;
+            }
+        } else if (t >= D.slot_words) {
+            __nanosleep(64);
+        }
+    }
+    atomicCAS(D.err, 0, kErrTimeout);
+    return -1;
+}
 
 __device__ __forceinline__ unsigned pack2(int lo, int hi) {
     return (unsigned)(lo & 0xffff) | ((unsigned)hi << 16);
@@ -92,12 +130,22 @@ __device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R
 // host gives each job blocks in proportion to its work); block: W warps.
 // Dynamic shared memory: the query profile, (K + 1) * mpad bytes,
 // mpad = passes * 32 * R.
-template <int R, int W>
+template <int R, int W, bool OVERSUB>
 __global__ void __launch_bounds__(W * 32)
 db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                 const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {
     extern __shared__ __align__(16) int8_t prof[];
+    // OVERSUB: the grid may exceed the blocks that fit at once (the server's steps); blocks
+    // beyond the first wave share the scratch slots
+    int slot = (int)blockIdx.x;
+    if constexpr (OVERSUB) {
+        __shared__ int s_slot;
+        if (threadIdx.x == 0) s_slot = db_acquire_slot(D);
+        __syncthreads();
+        slot = s_slot;
+        if (slot < 0) return;
+    }
     int jlo = 0, jhi = njobs - 1;                 // last job with block0 <= blockIdx.x
     while (jlo < jhi) {
         const int mid = (jlo + jhi + 1) >> 1;
@@ -122,7 +170,7 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
     for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
     const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
     const int lane = threadIdx.x & 31;
-    const int gwarp = blockIdx.x * W + (threadIdx.x >> 5);
+    const int gwarp = slot * W + (threadIdx.x >> 5);
     uint2 *bnd = scratch + (size_t)gwarp * (size_t)D.maxlen;
     const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
     const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
@@ -214,6 +262,13 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                     J.scores[s] = max(0, mx[h] + go);
                 }
             }
+        }
+    }
+    if constexpr (OVERSUB) {                      // hand the slot to a later block
+        __syncthreads();                          // every warp is done with the slot's scratch
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAnd(D.slot_pool + slot / 32, ~(1u << (slot % 32)));
         }
     }
 }

@@ -77,7 +77,7 @@ struct sw_ctx {
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
     swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, colaux, tb,
-        tbbnd, runs, walk, misc, dbscratch, dbovf, dbjob, dbscores, topk;
+        tbbnd, runs, walk, misc, dbscratch, dbslots, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
     std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class
     swgb::KernelTimer timer;
@@ -116,6 +116,7 @@ int db_topk(sw_ctx *c, const int32_t *dscores, int64_t nseq, int k, int2 *dout);
 int db_shape(int K, int m);
 int db_resident_blocks(sw_ctx *c, int K, int m, int *out);
 int db_warps_per_block(int K, int m);
+int db_rows_per_pass(int K, int m);      // query rows per pass of the packed kernel for this launch shape
 int db_launch(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m);
 int db_view(const sw_db *db, DbView *v, int64_t *nseq, int32_t *max_code, int *device);
 int db_chunk_maxlen(const sw_db *db, int32_t pair0, int32_t pair1);

@@ -42,13 +42,33 @@ static __global__ void max_code_kernel(const uint8_t *s, long long len, int *out
 constexpr long long kMaxProfileSmem = 200 * 1024;
 
 template <int R, int W>
-int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m) {
-    auto kern = db_s16x2_kernel<R, W>;
+int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m) {
     constexpr int ROWS = 32 * R;
     const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
     const size_t smem = (size_t)(K + 1) * (size_t)mpad;
-    // boundary rows: one per warp
-    RC(c->dbscratch.ensure((size_t)nblocks * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false>, W * 32, smem));
+    int occ2 = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, db_s16x2_kernel<R, W, true>, W * 32, smem));
+    occ = std::min(occ, occ2);
+    if (occ < 1) return SW_ECUDA;
+    // boundary rows: one per warp of every block that can be resident at once; a grid larger
+    // than that (the server's steps) takes the kernel whose later blocks share the slots
+    DbView D = D0;
+    D.nslots = occ * c->nsm;
+    D.slot_words = (D.nslots + 31) / 32;
+    const bool over = nblocks > D.nslots;
+    RC(c->dbscratch.ensure((size_t)D.nslots * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    RC(c->dbslots.ensure((size_t)D.slot_words * sizeof(unsigned)));
+    D.slot_pool = static_cast<unsigned *>(c->dbslots.p);
+    D.err = static_cast<int *>(c->err.p);
+    D.spin_limit = c->spin_limit;
+    if (over) {
+        init_slot_pool_kernel<<<1, 64, 0, c->stream>>>(D.slot_pool, D.slot_words, D.nslots, D.nslots);
+        CU(cudaGetLastError());
+        ++c->launches;
+    }
+    auto kern = over ? db_s16x2_kernel<R, W, true> : db_s16x2_kernel<R, W, false>;
     const int kp = kt_begin(c, SW_KT_DB16);
     kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
                                                          static_cast<const DevScoring *>(c->scorings.p),
@@ -67,12 +87,14 @@ int resident_blocks(sw_ctx *c, int K, int m, int *out) {
     if ((long long)smem > kMaxProfileSmem) return SW_ERANGE;
     static int attr_set[64] = {0};
     if (c->device < 64 && !attr_set[c->device]) {
-        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxProfileSmem));
+        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxProfileSmem));
         attr_set[c->device] = 1;
     }
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W>, W * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false>, W * 32, smem));
     if (occ < 1) return SW_ECUDA;
     *out = occ * c->nsm;
     return SW_OK;
@@ -99,6 +121,8 @@ int swgb::db_resident_blocks(sw_ctx *c, int K, int m, int *out) {
 }
 
 int swgb::db_warps_per_block(int K, int m) { return db_shape(K, m) == 2 ? 32 : 8; }
+
+int swgb::db_rows_per_pass(int K, int m) { return 32 * (db_shape(K, m) == 1 ? 16 : 8); }
 
 int swgb::db_launch(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m) {
     switch (db_shape(K, m)) {

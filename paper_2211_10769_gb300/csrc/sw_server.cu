@@ -19,6 +19,7 @@
 #include "aux_kernels.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -31,6 +32,8 @@ using namespace swgb;
 
 
 namespace {
+
+constexpr double kOversub = 4.0;     // blocks per step, in units of the blocks resident at once
 
 struct Slot {
     bool active = false;
@@ -181,7 +184,12 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     int resident = 0;
     RC(db_resident_blocks(c, S->ds.K, (int)maxm, &resident));
     const int W = db_warps_per_block(S->ds.K, (int)maxm);
+    const int rows = db_rows_per_pass(S->ds.K, (int)maxm);
     const int chunk_pairs = p0 < np ? (np - p0 + stride - 1) / stride : 0;
+    // a request's work is its query padded to whole passes of `rows` rows
+    auto padded = [&](int64_t m) { return (double)((m + rows - 1) / rows) * rows; };
+    double sumpad = 0;
+    for (Slot *s : act) sumpad += padded(s->m);
     std::vector<DbJob> jobs;
     int nblocks = 0;
     for (Slot *s : act) {
@@ -190,8 +198,9 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
         j.m = (int32_t)s->m;
         j.scoring = 0;
         j.pair0 = p0; j.pair1 = p1; j.pair_stride = stride;
-        // blocks in proportion to the request's share of the step's work
-        const int share = (int)((double)resident * (double)s->m / (double)std::max<int64_t>(1, summ) + 0.5);
+        // blocks in proportion to the request's share of the step's work, kOversub times what
+        // fits at once: blocks of short jobs finish early and free their SMs for the others
+        const int share = (int)std::ceil(kOversub * resident * padded(s->m) / std::max(1.0, sumpad));
         const int nb = std::max(1, std::min(share, (chunk_pairs + W - 1) / W));
         j.block0 = nblocks;
         nblocks += nb;
@@ -208,12 +217,17 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     RC(upload_scorings(c, {S->ds}));
     CU(cudaMemcpyAsync(S->jobs.p, S->hjobs.p, jb, cudaMemcpyHostToDevice, c->stream));
     for (Slot *s : act) CU(cudaMemsetAsync(static_cast<int32_t *>(s->ctr.p) + 1, 0, sizeof(int32_t), c->stream));
+    RC(reset_err(c));
     if (chunk_pairs > 0) {
         DbView v = S->view;
         v.maxlen = std::max(1, db_chunk_maxlen(S->db, p0, p0 + 1));     // pairs are sorted longest first
         RC(db_launch(c, static_cast<const DbJob *>(S->jobs.p), (int)jobs.size(), nblocks, v, S->ds.K, (int)maxm));
     }
+    CU(cudaMemcpyAsync(c->stage3.p, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    int e = 0;
+    std::memcpy(&e, c->stage3.p, sizeof(int));
+    RC(map_kernel_error(e));
     S->cur_chunk = (S->cur_chunk + 1) % S->chunks;
     for (Slot *s : act) {
         if (++s->visited >= S->chunks) RC(retire(S, *s));
