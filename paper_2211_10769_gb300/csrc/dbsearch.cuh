@@ -46,8 +46,11 @@ struct DbView {
     const uint8_t *res;        // all residues
     const int64_t *off;        // subject s = res[off[s] .. off[s+1])
     const int32_t *pairs;      // pair p = subjects pairs[2p], pairs[2p+1] (-1 = none)
+    const uint16_t *pres;      // pair p's residues interleaved, column j at pres[poff[p] + j]:
+    const int64_t *poff;       // low byte subject A, high byte subject B, 0xff past a subject's end;
+                               // n_p = poff[p+1] - poff[p] - 1 columns plus one padding column
     int32_t npairs;
-    int32_t maxlen;
+    int32_t maxlen;            // longest subject (scratch rows hold maxlen + 1 entries)
     // scratch slots: one per block that can be resident at a time (nslots = SMs x blocks per
     // SM); block b < nslots uses slot b, a later block (an oversubscribed grid) takes a slot a
     // finished block has released
@@ -57,6 +60,24 @@ struct DbView {
     long long spin_limit;      // bound of the wait for a free slot
     int *err;                  // error word (kErr*)
 };
+
+// Interleaved residues of every pair (see DbView::pres): one warp per pair.
+static __global__ void pair_residues_kernel(const uint8_t *res, const int64_t *off, const int32_t *pairs,
+                                            const int64_t *poff, int npairs, uint16_t *pres) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); p < npairs; p += nw) {
+        const int sa = pairs[2 * p], sb = pairs[2 * p + 1];
+        const int64_t a0 = off[sa], na = off[sa + 1] - a0;
+        const int64_t b0 = sb >= 0 ? off[sb] : 0, nb = sb >= 0 ? off[sb + 1] - b0 : 0;
+        const int64_t base = poff[p], cols = poff[p + 1] - base;   // n_p + 1
+        for (int64_t j = lane; j < cols; j += 32) {
+            const unsigned ca = j < na ? res[a0 + j] : 0xffu;
+            const unsigned cb = j < nb ? res[b0 + j] : 0xffu;
+            pres[base + j] = (uint16_t)(ca | (cb << 8));
+        }
+    }
+}
 
 // Presets the slot pool: the first wave's slots are taken, slots that do not exist too.
 static __global__ void init_slot_pool_kernel(unsigned *pool, int words, int nslots, int first_wave) {
@@ -130,8 +151,75 @@ __device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R
 // host gives each job blocks in proportion to its work); block: W warps.
 // Dynamic shared memory: the query profile, (K + 1) * mpad bytes,
 // mpad = passes * 32 * R.
+constexpr int kDbCH = 8;      // steps per chunk of the packed fill (steady chunks skip all range tests)
+
+// Per-lane state of the packed fill: U = H - open and E of the lane's R query
+// rows for both subjects (16-bit halves), the bottom row's (U, F) of the
+// previous step, the diagonal, the running maximum, and the prefetched
+// residue pair / top cell of the next step.
+template <int R>
+struct DbLane {
+    unsigned U[R], E[R];
+    unsigned ub, fb, udiag0, cmax;
+    unsigned cp;                 // residue pair of this step's column
+    uint2 topv;                  // (U, F) of the row above, lane 0 (passes after the first)
+    const int8_t *prow;          // this lane's profile rows of the current pass
+};
+
+// One step of the packed fill: column j = s - lane of both subjects.  CHECK
+// handles columns outside the pair (the first and last 31 steps).
+template <int R, bool CHECK>
+__device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, const uint16_t *pr, uint2 *bnd,
+                                        bool tops, bool last, int K, int mpad,
+                                        unsigned nge2, unsigned ngo2, unsigned neg2)
+{
+    const int j = s - lane;
+    unsigned uup = __shfl_up_sync(kFull, st.ub, 1);
+    unsigned fup = __shfl_up_sync(kFull, st.fb, 1);
+    if (lane == 0) { uup = st.topv.x; fup = st.topv.y; }
+    // inputs of the next step
+    const int jn = j + 1;
+    unsigned cpn;
+    uint2 topn = make_uint2(ngo2, neg2);
+    if (CHECK) {
+        cpn = (jn >= 0 && jn <= n) ? pr[jn] : 0xffffu;
+        if (tops && s + 1 < n) topn = bnd[s + 1];
+    } else {
+        cpn = pr[jn];                                   // jn <= n: at most the padding column
+        if (tops) topn = bnd[s + 1];                    // s + 1 <= n: inside the scratch row
+    }
+    if (!CHECK || (j >= 0 && j < n)) {
+        uint32_t wa[R / 4], wb[R / 4];
+        load_prof_words<R>(st.prow + min((int)(st.cp & 0xffu), K) * mpad, wa);
+        load_prof_words<R>(st.prow + min((int)(st.cp >> 8), K) * mpad, wb);
+        unsigned udiag = st.udiag0;
+        st.udiag0 = uup;
+        unsigned f = __viaddmax_s16x2(fup, nge2, uup);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const unsigned sp = merge_row(wa, wb, r);
+            const unsigned uold = st.U[r];
+            const unsigned e = __viaddmax_s16x2(st.E[r], nge2, uold);
+            const unsigned x = __viaddmax_s16x2_relu(udiag, sp, e);
+            const unsigned xgo = __viaddmax_s16x2(x, ngo2, neg2);   // x - open
+            const unsigned u = __viaddmax_s16x2(f, ngo2, xgo);      // H - open
+            st.E[r] = e;
+            udiag = uold;
+            st.U[r] = u;
+            if (r + 1 < R) f = __viaddmax_s16x2(f, nge2, xgo);
+        }
+        st.ub = st.U[R - 1];
+        st.fb = f;
+#pragma unroll
+        for (int r = 0; r + 1 < R; r += 2) st.cmax = __vimax3_s16x2(st.cmax, st.U[r], st.U[r + 1]);
+        if (!last && lane == 31) bnd[j] = make_uint2(st.ub, st.fb);
+    }
+    st.cp = cpn;
+    st.topv = topn;
+}
+
 template <int R, int W, bool OVERSUB>
-__global__ void __launch_bounds__(W * 32)
+__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : (R >= 16 ? 3 : 4))
 db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                 const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {
@@ -171,7 +259,7 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
     const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
     const int lane = threadIdx.x & 31;
     const int gwarp = slot * W + (threadIdx.x >> 5);
-    uint2 *bnd = scratch + (size_t)gwarp * (size_t)D.maxlen;
+    uint2 *bnd = scratch + (size_t)gwarp * (size_t)(D.maxlen + 1);
     const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
     const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
 
@@ -181,64 +269,34 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
         p = __shfl_sync(kFull, p, 0);
         if (p >= J.pair1) break;
         const int sa = D.pairs[2 * p], sb = D.pairs[2 * p + 1];
-        const uint8_t *ra = D.res + D.off[sa];
-        const int na = (int)(D.off[sa + 1] - D.off[sa]);
-        const uint8_t *rb = sb >= 0 ? D.res + D.off[sb] : ra;
-        const int nb = sb >= 0 ? (int)(D.off[sb + 1] - D.off[sb]) : 0;
-        const int n = max(na, nb);
+        const uint16_t *pr = D.pres + D.poff[p];
+        const int n = (int)(D.poff[p + 1] - D.poff[p]) - 1;     // columns (pr[n]: padding)
         unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
         for (int pass = 0; pass < passes; ++pass) {
-            const int8_t *prow = prof + pass * ROWS + lane * R;
-            unsigned U[R], E[R];
+            DbLane<R> st;
+            st.prow = prof + pass * ROWS + lane * R;
 #pragma unroll
-            for (int r = 0; r < R; ++r) { U[r] = ngo2; E[r] = neg2; }
-            unsigned ub = ngo2, fb = neg2, udiag0 = ngo2;
+            for (int r = 0; r < R; ++r) { st.U[r] = ngo2; st.E[r] = neg2; }
+            st.ub = ngo2; st.fb = neg2; st.udiag0 = ngo2;
+            st.cmax = cmax;
             const bool last = pass + 1 == passes;
-            // prefetched residues of this lane's column
-            int j = -lane;
-            int ca = (j >= 0 && j < na) ? ra[j] : K;
-            int cb = (j >= 0 && j < nb) ? rb[j] : K;
-            uint2 topv = (pass > 0 && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
-            for (int s = 0; s < n + 31; ++s) {
-                j = s - lane;
-                unsigned uup = __shfl_up_sync(kFull, ub, 1);
-                unsigned fup = __shfl_up_sync(kFull, fb, 1);
-                if (lane == 0) { uup = topv.x; fup = topv.y; }
-                const int jn = j + 1;
-                const int can = (jn >= 0 && jn < na) ? ra[jn] : K;
-                const int cbn = (jn >= 0 && jn < nb) ? rb[jn] : K;
-                uint2 topn = make_uint2(ngo2, neg2);
-                if (pass > 0 && s + 1 < n) topn = bnd[s + 1];
-                if (j >= 0 && j < n) {
-                    uint32_t wa[R / 4], wb[R / 4];
-                    load_prof_words<R>(prow + min(ca, K) * mpad, wa);
-                    load_prof_words<R>(prow + min(cb, K) * mpad, wb);
-                    unsigned udiag = udiag0;
-                    udiag0 = uup;
-                    unsigned f = __viaddmax_s16x2(fup, nge2, uup);
+            const bool tops = pass > 0;
+            // prefetched inputs of this lane's first column and of lane 0's first top cell
+            st.cp = lane == 0 && n > 0 ? pr[0] : 0xffffu;
+            st.topv = (tops && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
+            for (int s0 = 0; s0 < n + 31; s0 += kDbCH) {
+                if (s0 >= 31 && s0 + kDbCH <= n) {
+                    // steady state: every lane's column is inside the pair, the prefetched
+                    // column at most the padding column n
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const unsigned sp = merge_row(wa, wb, r);
-                        const unsigned uold = U[r];
-                        const unsigned e = __viaddmax_s16x2(E[r], nge2, uold);
-                        const unsigned x = __viaddmax_s16x2_relu(udiag, sp, e);
-                        const unsigned xgo = __viaddmax_s16x2(x, ngo2, neg2);   // x - open
-                        const unsigned u = __viaddmax_s16x2(f, ngo2, xgo);      // H - open
-                        E[r] = e;
-                        udiag = uold;
-                        U[r] = u;
-                        if (r + 1 < R) f = __viaddmax_s16x2(f, nge2, xgo);
-                    }
-                    ub = U[R - 1];
-                    fb = f;
-#pragma unroll
-                    for (int r = 0; r + 1 < R; r += 2) cmax = __vimax3_s16x2(cmax, U[r], U[r + 1]);
-                    if (!last && lane == 31) bnd[j] = make_uint2(ub, fb);
+                    for (int k = 0; k < kDbCH; ++k)
+                        db_step<R, false>(st, s0 + k, lane, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+                } else {
+                    for (int k = 0; k < kDbCH && s0 + k < n + 31; ++k)
+                        db_step<R, true>(st, s0 + k, lane, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
                 }
-                ca = can;
-                cb = cbn;
-                topv = topn;
             }
+            cmax = st.cmax;
             __syncwarp();
         }
         // warp maximum of each half

@@ -25,7 +25,7 @@ struct sw_db {
     int32_t max_code = -1;
     std::vector<int64_t> off;           // host copy of the offsets
     std::vector<int32_t> hpairs;        // host copy of the length-sorted pairs
-    DevBuf res, doff, pairs;
+    DevBuf res, doff, pairs, pres, poff;   // pres / poff: interleaved residues of every pair
 };
 
 namespace {
@@ -58,7 +58,7 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     D.nslots = occ * c->nsm;
     D.slot_words = (D.nslots + 31) / 32;
     const bool over = nblocks > D.nslots;
-    RC(c->dbscratch.ensure((size_t)D.nslots * W * (size_t)std::max(1, D.maxlen) * sizeof(uint2)));
+    RC(c->dbscratch.ensure((size_t)D.nslots * W * (size_t)(D.maxlen + 1) * sizeof(uint2)));
     RC(c->dbslots.ensure((size_t)D.slot_words * sizeof(unsigned)));
     D.slot_pool = static_cast<unsigned *>(c->dbslots.p);
     D.err = static_cast<int *>(c->err.p);
@@ -109,7 +109,7 @@ int resident_blocks(sw_ctx *c, int K, int m, int *out) {
 int swgb::db_shape(int K, int m) {
     const long long prof8 = (long long)(K + 1) * (((m + 255) / 256) * 256);
     if (prof8 > 96 * 1024) return 2;
-    return m >= 1024 ? 1 : 0;
+    return m > 256 ? 1 : 0;                 // 16 rows a lane once a query fills more than one 256-row pass
 }
 
 int swgb::db_resident_blocks(sw_ctx *c, int K, int m, int *out) {
@@ -136,6 +136,8 @@ int swgb::db_view(const sw_db *db, DbView *v, int64_t *nseq, int32_t *max_code, 
     v->res = static_cast<const uint8_t *>(db->res.p);
     v->off = static_cast<const int64_t *>(db->doff.p);
     v->pairs = static_cast<const int32_t *>(db->pairs.p);
+    v->pres = static_cast<const uint16_t *>(db->pres.p);
+    v->poff = static_cast<const int64_t *>(db->poff.p);
     v->npairs = db->npairs;
     v->maxlen = db->maxlen;
     *nseq = db->nseq;
@@ -190,12 +192,32 @@ extern "C" int sw_db_create(sw_ctx *c, const uint8_t *residues, const int64_t *o
     db->hpairs = pairs;
     rc = db->pairs.ensure(std::max<size_t>(1, pairs.size()) * sizeof(int32_t));
     if (rc) { delete db; return rc; }
+    // interleaved residues of the pairs: max(na, nb) columns plus one padding column each
+    std::vector<int64_t> poff((size_t)db->npairs + 1, 0);
+    for (int32_t p = 0; p < db->npairs; ++p) {
+        const int32_t sa = pairs[2 * (size_t)p], sb = pairs[2 * (size_t)p + 1];
+        const int64_t na = offsets[sa + 1] - offsets[sa];
+        const int64_t nb = sb >= 0 ? offsets[sb + 1] - offsets[sb] : 0;
+        poff[(size_t)p + 1] = poff[(size_t)p] + std::max(na, nb) + 1;
+    }
+    rc = db->pres.ensure(std::max<size_t>(1, (size_t)poff.back()) * sizeof(uint16_t));
+    if (!rc) rc = db->poff.ensure(poff.size() * sizeof(int64_t));
+    if (rc) { delete db; return rc; }
     const cudaMemcpyKind kind = is_device_ptr(residues) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     bool ok = true;
     if (total > 0) ok &= cudaMemcpyAsync(db->res.p, residues, (size_t)total, kind, c->stream) == cudaSuccess;
     ok &= cudaMemcpyAsync(db->doff.p, offsets, (size_t)(nseq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
     if (!pairs.empty())
         ok &= cudaMemcpyAsync(db->pairs.p, pairs.data(), pairs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    ok &= cudaMemcpyAsync(db->poff.p, poff.data(), poff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (ok && db->npairs > 0) {
+        pair_residues_kernel<<<(unsigned)std::min<long long>((db->npairs + 7) / 8, 16LL * c->nsm), 256, 0, c->stream>>>(
+            static_cast<const uint8_t *>(db->res.p), static_cast<const int64_t *>(db->doff.p),
+            static_cast<const int32_t *>(db->pairs.p), static_cast<const int64_t *>(db->poff.p), db->npairs,
+            static_cast<uint16_t *>(db->pres.p));
+        ok &= cudaGetLastError() == cudaSuccess;
+        ++c->launches;
+    }
     // largest residue code, checked against the alphabet at search time
     ok &= c->misc.ensure(sizeof(int)) == SW_OK;
     ok &= cudaMemsetAsync(c->misc.p, 0, sizeof(int), c->stream) == cudaSuccess;
@@ -245,6 +267,8 @@ int swgb::db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m,
     D.res = static_cast<const uint8_t *>(db->res.p);
     D.off = static_cast<const int64_t *>(db->doff.p);
     D.pairs = static_cast<const int32_t *>(db->pairs.p);
+    D.pres = static_cast<const uint16_t *>(db->pres.p);
+    D.poff = static_cast<const int64_t *>(db->poff.p);
     D.npairs = db->npairs;
     D.maxlen = db->maxlen;
     int32_t nflag = 0;
