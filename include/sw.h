@@ -181,9 +181,12 @@ int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8
                      const sw_scoring *sc, sw_hit *out);
 
 /*
- * Batched pairwise scores (many pairs of uneven lengths in one launch; the
- * paper's Section 3.1 replaces SW#'s static block sizes by sizes derived from
- * the sequence lengths, which this batch planner does per pair).  Pair p is
+ * Batched pairwise scores (many pairs of uneven lengths; the paper's Section
+ * 3.1 replaces SW#'s static block sizes by sizes derived from the sequence
+ * lengths, which this batch planner does per length bin).  Pairs are binned
+ * by scoring scheme and by query length (up to 1024 rows, longer); each bin
+ * is one launch with its own tile shape, and the bins' launches run
+ * concurrently.  Pair p is
  * a = a_res[a_off[p] .. a_off[p+1]) against b = b_res[b_off[p] .. b_off[p+1])
  * scored with scorings[scoring_of_pair[p]]; a_off / b_off are host arrays of
  * npairs + 1 entries starting at 0; residues may be host or device memory
@@ -192,8 +195,9 @@ int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8
  *
  * A plan keeps the inputs and the task table on the device:
  *   SW_BATCH_GRAPH     capture each run in a CUDA graph once and replay it;
- *   SW_BATCH_AUTOTUNE  time the candidate tile shapes on this plan and keep
- *                      the fastest (cached in the context per size class).
+ *   SW_BATCH_AUTOTUNE  time the candidate tile shapes of every bin on this plan
+ *                      and keep the fastest (cached in the context per bin
+ *                      size class).
  * sw_batch_run writes npairs hits (host memory).  A plan belongs to its
  * context and must be destroyed before it.
  */
@@ -205,7 +209,8 @@ int sw_batch_create(sw_ctx *ctx, int64_t npairs, const uint8_t *a_res, const int
                     int32_t nscorings, const sw_scoring *scorings, int32_t flags, sw_batch **out);
 int sw_batch_run(sw_batch *plan, sw_hit *out);
 void sw_batch_destroy(sw_batch *plan);
-/* Tile shape the plan runs with: rows per lane and compute warps per block. */
+/* Tile shape of the plan's largest bin (by cells): rows per lane and compute
+ * warps per block. */
 int sw_batch_config(const sw_batch *plan, int32_t *rows_per_lane, int32_t *warps);
 /* One-shot: create (no graph, no autotuning), run, destroy. */
 int sw_score_batch(sw_ctx *ctx, int64_t npairs, const uint8_t *a_res, const int64_t *a_off,

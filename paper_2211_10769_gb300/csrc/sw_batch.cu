@@ -1,16 +1,18 @@
-// sw_batch.cu -- many pairs of uneven lengths in one launch.
+// sw_batch.cu -- many pairs of uneven lengths, binned by length and scoring.
 //
-// Every pair is one task of the wavefront fill (its own scoring scheme:
-// DNA and protein pairs mix freely).  Tasks are ordered by cell count,
-// largest first, so the long pairs' strip pipelines start first and the
-// short pairs fill the device at the end (longest-processing-time order);
-// a strip only activates the warps that hold rows of its task.  A plan
-// keeps its inputs and task table on the device; its run (counter resets,
-// the fill, the per-task reduction and the scatter of results back to pair
-// order, the copy to the host) can be captured once in a CUDA graph and
-// replayed.  The tile shape is picked per plan from a small candidate set
-// by timing the plan itself (autotuning), and the choice is cached in the
-// context for plans of the same size class.
+// Every pair is one task of the wavefront fill.  Pairs are binned by their
+// scoring scheme (so each launch knows its alphabet: small alphabets get the
+// int32 query profile) and by their length in rows (short queries and long
+// ones want different strip heights); each bin is one launch of all its
+// tasks, ordered by cell count, largest first, so the long pairs' strip
+// pipelines start first and the short pairs fill the device at the end
+// (longest-processing-time order); a strip only activates the warps that
+// hold rows of its task.  A plan keeps its inputs and task table on the
+// device; its run (counter resets, the bins' fills, the per-task reduction,
+// the scatter of results back to pair order, the copy to the host) can be
+// captured once in a CUDA graph and replayed.  Each bin's tile shape is
+// picked from a candidate set by timing the plan itself (autotuning), and
+// the choice is cached in the context for bins of the same size class.
 #include "sw.h"
 #include "sw_ctx.h"
 #include "wavefront.cuh"
@@ -48,7 +50,23 @@ static __global__ void scatter_hits_kernel(const int4 *res, const int32_t *pair,
     if (k < ntasks) out[pair[k]] = res[k];
 }
 
-const FillConfig kCandidates[] = {{8, 4}, {4, 4}, {16, 4}, {8, 8}};
+const FillConfig kCandidates[] = {{8, 4}, {4, 4}, {12, 4}, {16, 4}, {8, 8}};
+
+constexpr int64_t kShortRows = 1024;      // row classes: queries up to this many rows, and longer
+
+// ticket counter of bin b starts at the bin's first ticket
+static __global__ void set_counters_kernel(unsigned long long *ctr, const long long *base, int nbins) {
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) ctr[b] = (unsigned long long)base[b];
+}
+
+struct Bin {
+    int32_t sidx = 0;              // scoring scheme of its pairs
+    int rclass = 0;                // 0: up to kShortRows rows, 1: longer
+    std::vector<int32_t> pairs;    // its pairs, largest first
+    FillConfig cfg{8, 4};
+    int t0 = 0, nt = 0;            // its tasks
+    long long tbase = 0, tcount = 0;
+};
 
 }  // namespace
 
@@ -62,75 +80,98 @@ struct sw_batch {
     std::vector<int64_t> aoff, boff;
     DevBuf a_own, b_own, tasks, prog, cand, res, hits, perm, bnd, ticket, meta;
     HostBuf host_hits;
-    FillConfig cfg{8, 4};
+    std::vector<Bin> bins;
+    FillConfig cfg{8, 4};          // the tile shape of the bin with the most cells
     bool fold = true;
     int maxK = 1;
     int ntasks = 0;
     long long tickets = 0;
     int grid = 0;
     cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> bstreams;   // one per bin: the bins' fills run concurrently
+    std::vector<cudaEvent_t> bevents;     // [0]: fork, [1 + k]: bin k done
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool use_graph = false;
     ~sw_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : bevents) if (e) cudaEventDestroy(e);
+        for (cudaStream_t t : bstreams) if (t) cudaStreamDestroy(t);
         if (stream) cudaStreamDestroy(stream);
     }
 };
 
 namespace {
 
-// Tasks for tile shape cfg: pairs with cells, largest first.
-int build_tasks(sw_batch *B, const FillConfig &cfg) {
-    const int HC = fill_rows_per_strip(cfg);
-    std::vector<int32_t> order;
-    for (int64_t p = 0; p < B->npairs; ++p)
-        if (B->m[(size_t)p] > 0 && B->n[(size_t)p] > 0) order.push_back((int32_t)p);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return (double)B->m[(size_t)x] * (double)B->n[(size_t)x] > (double)B->m[(size_t)y] * (double)B->n[(size_t)y];
-    });
+// Task table of the plan: the bins in order, each bin's pairs largest first
+// with the bin's tile shape; tickets numbered across the whole plan.
+int build_plan(sw_batch *B) {
     std::vector<FillTask> tasks;
-    tasks.reserve(order.size());
-    long long tickets = 0;
+    std::vector<int32_t> order;
+    std::vector<long long> bases;
     size_t bnd_need = 0;
-    for (int32_t p : order) {
-        const int ns = (int)((B->m[(size_t)p] + HC - 1) / HC);
-        if (ns > 1) bnd_need += 2 * (size_t)B->n[(size_t)p] * sizeof(int2);
+    for (const Bin &bin : B->bins) {
+        const int HC = fill_rows_per_strip(bin.cfg);
+        for (int32_t p : bin.pairs)
+            if ((B->m[(size_t)p] + HC - 1) / HC > 1) bnd_need += 2 * (size_t)B->n[(size_t)p] * sizeof(int2);
     }
     RC(B->bnd.ensure(std::max<size_t>(bnd_need, 16)));
     size_t boff = 0;
-    for (int32_t p : order) {
-        FillTask t{};
-        t.a = B->da + B->aoff[(size_t)p];
-        t.b = B->db + B->boff[(size_t)p];
-        t.rows = (int32_t)B->m[(size_t)p];
-        t.ncols = (int32_t)B->n[(size_t)p];
-        t.nstrips = (t.rows + HC - 1) / HC;
-        t.scoring = B->sidx[(size_t)p];
-        t.ticket0 = tickets;
-        t.nslot = 2;
-        if (t.nstrips > 1) {
-            t.bnd = reinterpret_cast<int2 *>(static_cast<char *>(B->bnd.p) + boff);
-            boff += 2 * (size_t)t.ncols * sizeof(int2);
+    long long tickets = 0;
+    B->cfg = B->bins.empty() ? FillConfig{8, 4} : B->bins[0].cfg;
+    double best_cells = -1;
+    for (Bin &bin : B->bins) {
+        const int HC = fill_rows_per_strip(bin.cfg);
+        bin.t0 = (int)tasks.size();
+        bin.tbase = tickets;
+        double cells = 0;
+        for (int32_t p : bin.pairs) {
+            FillTask t{};
+            t.a = B->da + B->aoff[(size_t)p];
+            t.b = B->db + B->boff[(size_t)p];
+            t.rows = (int32_t)B->m[(size_t)p];
+            t.ncols = (int32_t)B->n[(size_t)p];
+            t.nstrips = (t.rows + HC - 1) / HC;
+            t.scoring = B->sidx[(size_t)p];
+            t.ticket0 = tickets;
+            t.nslot = 2;
+            if (t.nstrips > 1) {
+                t.bnd = reinterpret_cast<int2 *>(static_cast<char *>(B->bnd.p) + boff);
+                boff += 2 * (size_t)t.ncols * sizeof(int2);
+            }
+            tickets += t.nstrips;
+            cells += (double)t.rows * (double)t.ncols;
+            tasks.push_back(t);
+            order.push_back(p);
         }
-        tickets += t.nstrips;
-        tasks.push_back(t);
+        bin.nt = (int)tasks.size() - bin.t0;
+        bin.tcount = tickets - bin.tbase;
+        bases.push_back(bin.tbase);
+        if (cells > best_cells) { best_cells = cells; B->cfg = bin.cfg; }
     }
     B->ntasks = (int)tasks.size();
     B->tickets = tickets;
-    B->cfg = cfg;
     const size_t tb = std::max<size_t>(1, tasks.size()) * sizeof(FillTask);
     RC(B->tasks.ensure(tb));
     RC(B->prog.ensure(std::max<long long>(1, tickets) * sizeof(int)));
     RC(B->cand.ensure(std::max<long long>(1, tickets) * sizeof(int4)));
     RC(B->res.ensure(std::max<size_t>(1, tasks.size()) * sizeof(int4)));
     RC(B->perm.ensure(std::max<size_t>(1, order.size()) * sizeof(int32_t)));
+    // counters and error word: [bins x u64 counters][bins x i64 bases][err]
+    const size_t nb = std::max<size_t>(1, B->bins.size());
+    RC(B->ticket.ensure(16 * nb + 256));
     if (!tasks.empty()) {
         CU(cudaMemcpy(B->tasks.p, tasks.data(), tb, cudaMemcpyHostToDevice));
         CU(cudaMemcpy(B->perm.p, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(static_cast<char *>(B->ticket.p) + 8 * nb, bases.data(), bases.size() * sizeof(long long),
+                      cudaMemcpyHostToDevice));
     }
     return SW_OK;
+}
+
+int *batch_err(sw_batch *B) {
+    return reinterpret_cast<int *>(static_cast<char *>(B->ticket.p) + 16 * std::max<size_t>(1, B->bins.size()) + 64);
 }
 
 // Enqueue one run of the plan on B->stream (graph-capturable: no host sync,
@@ -140,24 +181,46 @@ int enqueue_run(sw_batch *B) {
     cudaStream_t st = B->stream;
     const size_t out_bytes = (size_t)std::max<int64_t>(1, B->npairs) * sizeof(int4);
     CU(cudaMemsetAsync(B->hits.p, 0, out_bytes, st));
+    const size_t nb = std::max<size_t>(1, B->bins.size());
+    CU(cudaMemsetAsync(batch_err(B), 0, sizeof(int), st));
     if (B->ntasks > 0) {
         CU(cudaMemsetAsync(B->prog.p, 0, (size_t)B->tickets * sizeof(int), st));
-        CU(cudaMemsetAsync(B->ticket.p, 0, 256, st));            // ticket counter and error word
-        FillLaunch L;
-        L.tasks = static_cast<const FillTask *>(B->tasks.p);
-        L.scorings = static_cast<const DevScoring *>(B->meta.p);
-        L.ticket = static_cast<unsigned long long *>(B->ticket.p);
-        L.prog = static_cast<int *>(B->prog.p);
-        L.cand = static_cast<int4 *>(B->cand.p);
-        L.err = reinterpret_cast<int *>(static_cast<char *>(B->ticket.p) + 64);
-        L.total = B->tickets;
-        L.spin_limit = c->spin_limit;
-        L.ntasks = B->ntasks;
+        unsigned long long *ctr = static_cast<unsigned long long *>(B->ticket.p);
+        set_counters_kernel<<<1, 32, 0, st>>>(ctr, reinterpret_cast<const long long *>(ctr + nb), (int)B->bins.size());
+        CU(cudaGetLastError());
+        ++c->launches;
+        // fork: every bin's fill on its own stream, so the bins' tails overlap
+        CU(cudaEventRecord(B->bevents[0], st));
         cudaStream_t saved = c->stream;
-        c->stream = st;
-        const int rc = launch_fill(c, B->cfg, kModeScore, B->fold, L, B->maxK, B->tickets);
+        int rc = SW_OK;
+        for (size_t k = 0; k < B->bins.size() && rc == SW_OK; ++k) {
+            const Bin &bin = B->bins[k];
+            cudaStream_t bs = B->bstreams[k];
+            if (cudaStreamWaitEvent(bs, B->bevents[0], 0) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; break; }
+            if (bin.nt > 0) {
+                const DevScoring &sc = B->scorings[(size_t)bin.sidx];
+                FillLaunch L;
+                L.tasks = static_cast<const FillTask *>(B->tasks.p) + bin.t0;
+                L.scorings = static_cast<const DevScoring *>(B->meta.p);
+                L.ticket = ctr + k;
+                L.prog = static_cast<int *>(B->prog.p);
+                L.cand = static_cast<int4 *>(B->cand.p);
+                L.err = batch_err(B);
+                L.total = bin.tbase + bin.tcount;
+                L.spin_limit = c->spin_limit;
+                L.ntasks = bin.nt;
+                c->stream = bs;
+                rc = launch_fill(c, bin.cfg, kModeScore, fold_open(sc), L, sc.K, bin.tcount);
+                c->stream = saved;
+            }
+            if (rc == SW_OK && cudaEventRecord(B->bevents[1 + k], bs) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; }
+            if (rc == SW_OK && cudaStreamWaitEvent(st, B->bevents[1 + k], 0) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; }
+        }
         c->stream = saved;
         RC(rc);
+        FillLaunch L;
+        L.tasks = static_cast<const FillTask *>(B->tasks.p);
+        L.cand = static_cast<int4 *>(B->cand.p);
         reduce_candidates_kernel<<<(B->ntasks + 7) / 8, 256, 0, st>>>(L.tasks, B->ntasks, L.cand,
                                                                       static_cast<int4 *>(B->res.p));
         CU(cudaGetLastError());
@@ -169,8 +232,8 @@ int enqueue_run(sw_batch *B) {
         ++c->launches;
     }
     CU(cudaMemcpyAsync(B->host_hits.p, B->hits.p, out_bytes, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(static_cast<char *>(B->host_hits.p) + out_bytes,
-                       static_cast<char *>(B->ticket.p) + 64, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(static_cast<char *>(B->host_hits.p) + out_bytes, batch_err(B), sizeof(int),
+                       cudaMemcpyDeviceToHost, st));
     return SW_OK;
 }
 
@@ -185,13 +248,14 @@ int finish_run(sw_batch *B, sw_hit *out) {
     return SW_OK;
 }
 
-// Size class of a plan for the autotune cache: log2 of its cells and of its pair count.
-long long size_class(const sw_batch *B) {
+// Size class of a bin for the autotune cache: its alphabet, row class, and
+// log2 of its cells and of its pair count.
+long long bin_class(const sw_batch *B, const Bin &bin) {
     double cells = 0;
-    for (int64_t p = 0; p < B->npairs; ++p) cells += (double)B->m[(size_t)p] * (double)B->n[(size_t)p];
+    for (int32_t p : bin.pairs) cells += (double)B->m[(size_t)p] * (double)B->n[(size_t)p];
     const int lc = cells > 1 ? (int)std::log2(cells) : 0;
-    const int lp = B->npairs > 1 ? (int)std::log2((double)B->npairs) : 0;
-    return (long long)lc * 64 + lp + 4096LL * B->maxK;
+    const int lp = bin.pairs.size() > 1 ? (int)std::log2((double)bin.pairs.size()) : 0;
+    return (((long long)B->scorings[(size_t)bin.sidx].K * 2 + bin.rclass) * 64 + lc) * 64 + lp;
 }
 
 }  // namespace
@@ -281,32 +345,73 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
         CU(cudaStreamSynchronize(B->stream));
         if (e) return map_kernel_error(e);
     }
-    // tile shape: cached for the size class, else autotuned (or the context default)
-    const long long cls = size_class(B);
-    FillConfig cfg = c->bat;
-    bool tuned = false;
-    for (const auto &kv : c->batch_tune)
-        if (kv.first == cls) { cfg = kv.second; tuned = true; }
-    if (!tuned && (flags & SW_BATCH_AUTOTUNE)) {
-        float best = 1e30f;
+    // bins: scoring scheme x row class, the bin with the most cells first
+    {
+        std::vector<Bin> bins;
+        for (int64_t p = 0; p < npairs; ++p) {
+            if (B->m[(size_t)p] == 0 || B->n[(size_t)p] == 0) continue;
+            const int rcl = B->m[(size_t)p] > kShortRows ? 1 : 0;
+            Bin *bin = nullptr;
+            for (Bin &x : bins) if (x.sidx == B->sidx[(size_t)p] && x.rclass == rcl) bin = &x;
+            if (!bin) { bins.push_back(Bin{}); bin = &bins.back(); bin->sidx = B->sidx[(size_t)p]; bin->rclass = rcl; }
+            bin->pairs.push_back((int32_t)p);
+        }
+        auto cells = [&](int32_t p) { return (double)B->m[(size_t)p] * (double)B->n[(size_t)p]; };
+        for (Bin &bin : bins)
+            std::stable_sort(bin.pairs.begin(), bin.pairs.end(), [&](int32_t x, int32_t y) { return cells(x) > cells(y); });
+        auto bin_cells = [&](const Bin &bin) { double t = 0; for (int32_t p : bin.pairs) t += cells(p); return t; };
+        std::stable_sort(bins.begin(), bins.end(), [&](const Bin &x, const Bin &y) { return bin_cells(x) > bin_cells(y); });
+        for (Bin &bin : bins) bin.cfg = c->bat;
+        B->bins = std::move(bins);
+        for (size_t k = 0; k < B->bins.size(); ++k) {
+            cudaStream_t bs = nullptr;
+            CU(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+            B->bstreams.push_back(bs);
+        }
+        for (size_t k = 0; k < B->bins.size() + 1; ++k) {
+            cudaEvent_t e = nullptr;
+            CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            B->bevents.push_back(e);
+        }
+    }
+    // each bin's tile shape: cached for its size class, else autotuned one bin at a time
+    // (the others keep their current shapes), else the context default
+    std::vector<long long> cls(B->bins.size());
+    std::vector<bool> tuned(B->bins.size(), false);
+    for (size_t k = 0; k < B->bins.size(); ++k) {
+        cls[k] = bin_class(B, B->bins[k]);
+        for (const auto &kv : c->batch_tune)
+            if (kv.first == cls[k]) { B->bins[k].cfg = kv.second; tuned[k] = true; }
+    }
+    if (flags & SW_BATCH_AUTOTUNE) {
         cudaEvent_t e0, e1;
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
-        for (const FillConfig &cand : kCandidates) {
-            RC(build_tasks(B, cand));
-            CU(cudaEventRecord(e0, B->stream));
-            RC(enqueue_run(B));
-            CU(cudaEventRecord(e1, B->stream));
-            CU(cudaStreamSynchronize(B->stream));
-            float ms = 0;
-            CU(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; cfg = cand; }
+        int rc = SW_OK;
+        for (size_t k = 0; k < B->bins.size() && rc == SW_OK; ++k) {
+            if (tuned[k]) continue;
+            float best = 1e30f;
+            FillConfig pick = B->bins[k].cfg;
+            for (const FillConfig &cand : kCandidates) {
+                B->bins[k].cfg = cand;
+                rc = build_plan(B);
+                if (!rc) rc = cudaEventRecord(e0, B->stream) == cudaSuccess ? SW_OK : SW_ECUDA;
+                if (!rc) rc = enqueue_run(B);
+                if (!rc) rc = cudaEventRecord(e1, B->stream) == cudaSuccess ? SW_OK : SW_ECUDA;
+                if (!rc) rc = cudaStreamSynchronize(B->stream) == cudaSuccess ? SW_OK : SW_ECUDA;
+                float ms = 0;
+                if (!rc) rc = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? SW_OK : SW_ECUDA;
+                if (rc) break;
+                if (ms < best) { best = ms; pick = cand; }
+            }
+            B->bins[k].cfg = pick;
+            if (!rc) c->batch_tune.push_back({cls[k], pick});
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->batch_tune.push_back({cls, cfg});
+        if (rc) { cudaGetLastError(); return rc; }
     }
-    RC(build_tasks(B, cfg));
+    RC(build_plan(B));
     if (flags & SW_BATCH_GRAPH) {
         // one plain run first: kernel attributes are set outside the capture
         RC(enqueue_run(B));
@@ -331,7 +436,7 @@ extern "C" int sw_batch_run(sw_batch *B, sw_hit *out) {
     DeviceGuard g(B->c->device);
     if (B->use_graph) {
         CU(cudaGraphLaunch(B->exec, B->stream));
-        B->c->launches += B->ntasks > 0 ? 3 : 0;
+        B->c->launches += B->ntasks > 0 ? 3 + (int64_t)B->bins.size() : 0;
     } else {
         RC(enqueue_run(B));
     }
