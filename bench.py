@@ -69,6 +69,24 @@ def parse():
     return ap.parse_args()
 
 
+def slowest_rank_time(total, world, device):
+    """Timed-region seconds of the slowest rank (every rank gets it): replicas
+    run independently, so the job is done when the last one is."""
+    if world <= 1:
+        return total
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, slowest_total, steps):
+    """Units per second of the whole job: every rank's units over the slowest rank's time per step."""
+    return world * units_per_rank / (slowest_total / steps)
+
+
 def dist_init(n):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -186,12 +204,7 @@ def run_swgb(args, rank, world):
     kt = {name: ctx.kernel_time(kind) for name, kind in
           (("fill", binding.KT_FILL), ("fill_tb", binding.KT_FILL_TB), ("walk", binding.KT_WALK))}
     ctx.timing(False)
-    total = sum(times)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total = float(t.item())
+    total = slowest_rank_time(sum(times), world, "cuda")
 
     # dominant kernel: the forward wavefront fill, timed alone through sw_score
     fill_times = []
@@ -228,7 +241,7 @@ def run_swgb(args, rank, world):
         probe = probe_int_rates(ctx)
     out = {
         "metric": "GCUPS on 1 GB300 (exact scores); batched vs per-pair GCUPS; p50/p99 latency",
-        "value": round(world * cells / (total / args.steps) / 1e9, 2),
+        "value": round(whole_job_rate(cells, world, total, args.steps) / 1e9, 2),
         "unit": "GCUPS",
         "n_gpus": world,
         "steps": args.steps,
