@@ -341,6 +341,10 @@ wavefront_kernel(const FillLaunch L)
                 else prof[c * HC + lr] = (int8_t)v;
             }
         }
+        // the residue ring's last 32 slots read as padding: lanes may prefetch the columns
+        // left of the task (index -31 .. -1) during their first chunk (see virt_ok below);
+        // the input warp reaches those slots only after every warp has left its first chunk
+        if (threadIdx.x < 32) bring[QB - 32 + threadIdx.x] = (uint8_t)K;
         __syncthreads();
 
         if (warp == W) {
@@ -475,6 +479,9 @@ wavefront_kernel(const FillLaunch L)
 
             int seen_in = 0;
             bool loaded = false;             // inputs of step s0 were prefetched by the previous step
+            // columns left of the task may be computed (first chunk) only from a border state,
+            // and never in traceback mode (their decision words would land outside the tile)
+            const bool virt_ok = MODE != kModeTb && T.left == nullptr;
             int c;
             uint32_t pw[NPW];
             int2 top;
@@ -494,7 +501,11 @@ wavefront_kernel(const FillLaunch L)
                     top = rin[s0 & (QS - 1)];
                     loaded = true;
                 }
-                if (s0 >= 31 && s0 + CH + 1 <= n) {
+                // steady state: every lane's column and the prefetched one are in [0, n); a task
+                // entered from the matrix border also takes the first chunk this way, computing
+                // the columns left of the task with the padding residue: that keeps a lane at the
+                // border state (H = 0, E and F at -open, which give column 0 the same values)
+                if ((s0 >= 31 || virt_ok) && s0 + CH + 1 <= n) {
                     // steady state: every lane's column and the prefetched one are in [0, n)
 #pragma unroll kUnroll
                     for (int k = 0; k < CH; ++k) {
