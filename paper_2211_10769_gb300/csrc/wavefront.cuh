@@ -249,7 +249,8 @@ __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (
 
 // One wavefront step of one lane: column j = s - lane of its R rows.
 // CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
-// a sweep); the steady state skips those tests.
+// a sweep) where no padding stands in for them (traceback tiles, tasks with
+// a left boundary); every other step skips those tests.
 template <int R, int MODE, int PK, bool CHECK>
 __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int2 top,
                                           int s, int lane, int n, int go, int ge,
@@ -519,8 +520,30 @@ wavefront_kernel(const FillLaunch L)
                         for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
                     }
+                } else if (virt_ok) {
+                    // the sweep's last steps (and short sweeps): a lane right of the task reads
+                    // the padding residue and lane 0 an -inf row above, so every value such a
+                    // lane computes stays below the task's best cell and never reaches a real
+                    // one (lane l + 1 only reads lane l's column when it is its own); the steps
+                    // need no per-lane bounds test and run at the steady pace.  The last step
+                    // is n + 30: lane 31 writes the ring only for its real columns.
+#pragma unroll kUnroll
+                    for (int k = 0; k < CH; ++k) {
+                        const int s = s0 + k;
+                        if (s >= n + 31) break;
+                        const int jn = s + 1 - lane;
+                        const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
+                        const int2 topn = s + 1 < n ? rin[(s + 1) & (QS - 1)] : make_int2(kNeg, kNeg);
+                        uint32_t pwn[NPW];
+                        load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
+                        lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+#pragma unroll
+                        for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
+                        top = topn;
+                    }
                 } else {
-                    // the first and last 31 steps: the same prefetch, bounds-checked
+                    // traceback tiles and tasks with a left boundary: the first and last 31
+                    // steps with the same prefetch, bounds-checked
 #pragma unroll 1
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
