@@ -284,6 +284,7 @@ wavefront_kernel(const FillLaunch L)
     constexpr int HC = W * 32 * R;
     constexpr int CH = kCH, QS = kQS, QB = kQB, IOB = kIOB;
     static_assert(QS >= 2 * IOB + 2 * CH + 64, "ring too small");
+    static_assert(CH % kUnroll == 0, "chunks are whole unrolled groups");
 
     extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC scores of PB bytes
     constexpr int PB = PK == kProf32 ? 4 : 1;
@@ -492,8 +493,11 @@ wavefront_kernel(const FillLaunch L)
                     if (!warp_wait_geq(&prod[warp], need_in, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
                     seen_in = need_in;
                 }
-                const int out_hi = min(n, max(0, s0 + CH - 31));
-                if (out_hi > 0 && !warp_wait_geq(&cons[warp + 1], out_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
+                // lane 31 writes columns below s0 + CH - 31 to the ring this chunk (past n only
+                // on the padded path below); out_hi of them are real and get published
+                const int ring_hi = max(0, s0 + CH - 31);
+                const int out_hi = min(n, ring_hi);
+                if (ring_hi > 0 && !warp_wait_geq(&cons[warp + 1], ring_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
                 if (!loaded) {
                     // inputs of the sweep's first step (later steps prefetch the next one)
                     const int j = s0 - lane;
@@ -525,21 +529,26 @@ wavefront_kernel(const FillLaunch L)
                     // the padding residue and lane 0 an -inf row above, so every value such a
                     // lane computes stays below the task's best cell and never reaches a real
                     // one (lane l + 1 only reads lane l's column when it is its own); the steps
-                    // need no per-lane bounds test and run at the steady pace.  The last step
-                    // is n + 30: lane 31 writes the ring only for its real columns.
-#pragma unroll kUnroll
-                    for (int k = 0; k < CH; ++k) {
-                        const int s = s0 + k;
-                        if (s >= n + 31) break;
-                        const int jn = s + 1 - lane;
-                        const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
-                        const int2 topn = s + 1 < n ? rin[(s + 1) & (QS - 1)] : make_int2(kNeg, kNeg);
-                        uint32_t pwn[NPW];
-                        load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
-                        lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                    // need no per-lane bounds test.  Steps go in whole unrolled groups (a test
+                    // inside the unrolled body would keep it from unrolling), so up to
+                    // kUnroll - 1 steps run past the last one (n + 30) and lane 31 may write
+                    // columns n .. n + kUnroll - 2 to the ring: the wait on the consumer above
+                    // covers them.
+                    for (int g = 0; g < CH; g += kUnroll) {
+                        if (s0 + g >= n + 31) break;
 #pragma unroll
-                        for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
-                        top = topn;
+                        for (int k = 0; k < kUnroll; ++k) {
+                            const int s = s0 + g + k;
+                            const int jn = s + 1 - lane;
+                            const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
+                            const int2 topn = s + 1 < n ? rin[(s + 1) & (QS - 1)] : make_int2(kNeg, kNeg);
+                            uint32_t pwn[NPW];
+                            load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
+                            lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+#pragma unroll
+                            for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
+                            top = topn;
+                        }
                     }
                 } else {
                     // traceback tiles and tasks with a left boundary: the first and last 31
