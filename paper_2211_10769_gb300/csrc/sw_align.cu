@@ -53,13 +53,19 @@ int empty_alignment(sw_alignment *out) {
 
 template <typename Word, int R>
 int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT) {
-    if ((long long)nI * nJ > kWalkTableMax || BT < 32 * kLook) return SW_EINVAL;
+    if ((long long)nI * nJ > kWalkTableMax || BT < kWalkMinBT || BT % R != 0) return SW_EINVAL;
     TileTable<Word> T;
     T.bits = reinterpret_cast<const Word *const *>(table);
     T.I0 = I0; T.J0 = J0; T.nI = nI; T.nJ = nJ; T.BT = BT; T.R = R;
+    const size_t smem = walk_window_bytes<R>(sizeof(Word));
+    static bool attr_set = false;                        // per instantiation
+    if (!attr_set) {
+        CU(cudaFuncSetAttribute(walk_kernel<Word, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
     const int kp = kt_begin(c, SW_KT_WALK);
-    walk_kernel<Word, R><<<1, 32, 0, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
-                                                   static_cast<int2 *>(c->runs.p), kWalkMaxIters);
+    walk_kernel<Word, R><<<1, kWalkThreads, smem, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
+                                                               static_cast<int2 *>(c->runs.p), kWalkMaxIters);
     kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;

@@ -10,8 +10,16 @@
 //   state E: emit I, go left; back to H if the E-opened bit is set;
 //   state F: emit D, go up; back to H if the F-opened bit is set.
 //
-// One warp walks.  Runs are taken 64 cells at a time (each lane issues
-// two loads at once, so their latencies overlap): in state H the lanes
+// The walk is a chain of dependent lookups, so it reads them from shared
+// memory: the block stages a window of the decision words that follows the
+// diagonal through the walk's cell (kWinRows rows above it, kWinCols
+// columns per row group, kWinRight of them right of the diagonal), one
+// warp walks inside it, and the block stages the next window where the
+// walk left the last one.  The path of a pair worth aligning stays near a
+// diagonal, so a window holds several hundred of its cells; a long gap
+// only costs extra windows.
+//
+// One warp walks.  Runs are taken 64 cells at a time: in state H the lanes
 // read the cells of the diagonal ahead and the walk jumps over the leading
 // cells whose source is "diagonal"; in state E (F) they read the cells to
 // the left (above) and the walk jumps to the first one whose opened bit is
@@ -44,124 +52,224 @@ struct TileTable {
     int32_t R;                 // rows per word
 };
 
-constexpr int kLook = 2;           // groups of 32 cells each lane reads ahead per iteration (2 measured
-                                   // best of 1..16: runs are short, wasted look-ahead costs issue time)
+constexpr int kLook = 2;              // groups of 32 cells each lane reads ahead per iteration
 constexpr int kWalkTableMax = 4096;   // tile-table entries cached in shared memory
+constexpr int kWinRows = 768;         // rows of a window (a multiple of every R)
+constexpr int kWinCols = 128;         // columns a window keeps per row group
+constexpr int kWinRight = 64;         // ... of them right of the diagonal through the walk's cell
+constexpr int kWalkThreads = 256;     // threads staging a window (warp 0 also walks)
+constexpr int kStage = 16;            // window words a thread loads at once
+constexpr int kWalkMinBT = 1024;      // tiles at least this side: a window meets 2 x 2 tiles at most
 
-// Where the walk is: its cell's tile (absolute tile row / column) and the
-// cell's offsets inside that tile.  One division per iteration.
-struct WalkPos {
-    int I, J, li, lj;
+template <int R>
+constexpr size_t walk_window_bytes(size_t word_bytes) { return (size_t)(kWinRows / R) * kWinCols * word_bytes; }
+
+// Where a window lies (all coordinates 0-based).  Row groups g = 0 .. ng-1
+// hold rows r_lo + g*R .. r_lo + g*R + R - 1 (r_lo a multiple of R); group
+// g keeps columns [clo(g), clo(g) + kWinCols) with clo(g) = chi - (ng-1-g)*R,
+// so the kept band slides along the diagonal.  The window meets at most two
+// tile rows (the second from window row lrb on) and two tile columns (the
+// second from column cb on); tile (x, y) starts at row rbase[x], column
+// cbase[y], its words are tp[2x + y] and bit 2x + y of pres says whether it
+// was recomputed.
+struct WalkWindow {
+    int r_lo, ng, chi;
+    int lrb, cb;
+    int rbase[2], cbase[2];
+    int pres;
+    const void *tp[4];
 };
 
-// Decision nibble of the cell p steps back along (di, dj) from the walk's
-// cell, -2 at the matrix border, -1 in a tile that was not computed.  The
-// look-ahead (< BT) crosses at most one tile edge per direction.  The load
-// is unconditional (a cell without bits reads the valid word `dummy`
-// instead), so the loads of all look-ahead cells can be in flight together.
+template <typename Word>
+__device__ __forceinline__ const Word *tile_ptr(const TileTable<Word> &T, const Word *const *tiles, int I, int J) {
+    const int ti = I - T.I0, tj = J - T.J0;
+    return (ti >= 0 && tj >= 0 && ti < T.nI && tj < T.nJ) ? tiles[ti * T.nJ + tj] : nullptr;
+}
+
+// The window whose last row group holds the walk's cell (r0, c0), with that
+// cell kWinRight columns left of the group's last kept column.
 template <typename Word, int R>
-__device__ __forceinline__ int nibble_back(const TileTable<Word> &T, const Word *const *tiles, const WalkPos &P,
-                                           int i, int j, int di, int dj, int p, const Word *dummy) {
-    const int ci = i - di * p, cj = j - dj * p;
-    int I = P.I, J = P.J, li = P.li - di * p, lj = P.lj - dj * p;
-    if (li < 0) { li += T.BT; --I; }
-    if (lj < 0) { lj += T.BT; --J; }
-    I -= T.I0;
-    J -= T.J0;
-    const bool border = ci <= 0 || cj <= 0;
-    const bool inside = !border && I >= 0 && J >= 0 && I < T.nI && J < T.nJ;
-    const Word *b = inside ? tiles[I * T.nJ + J] : nullptr;
-    const bool have = b != nullptr;
-    const int lr = have ? li : 0;
-    const Word *addr = have ? b + (size_t)(lr / R) * (size_t)T.BT + lj : dummy;
-    const Word w = __ldcg(addr);
-    const int nib = (int)((unsigned long long)w >> (4 * (lr % R))) & 15;
-    return border ? -2 : (have ? nib : -1);
+__device__ WalkWindow make_window(const TileTable<Word> &T, const Word *const *tiles, int r0, int c0) {
+    constexpr int RG = kWinRows / R;
+    constexpr int kNone = 0x7fffffff;
+    WalkWindow m;
+    r0 = max(r0, 0);
+    c0 = max(c0, 0);
+    const int ghi = r0 / R, glo = max(0, ghi - (RG - 1));
+    m.ng = ghi - glo + 1;
+    m.r_lo = glo * R;
+    m.chi = c0 - (kWinCols - 1 - kWinRight);
+    const int BT = T.BT;
+    const int ia = m.r_lo / BT, ib = (ghi * R + R - 1) / BT;
+    m.lrb = ib > ia ? ib * BT - m.r_lo : kNone;
+    const int cmin = max(0, m.chi - (m.ng - 1) * R), cmax = max(0, m.chi + kWinCols - 1);
+    const int ja = cmin / BT, jb = cmax / BT;
+    m.cb = jb > ja ? jb * BT : kNone;
+    m.rbase[0] = ia * BT; m.rbase[1] = ib * BT;
+    m.cbase[0] = ja * BT; m.cbase[1] = jb * BT;
+    m.pres = 0;
+    for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) {
+            const Word *b = tile_ptr(T, tiles, x ? ib : ia, y ? jb : ja);
+            m.tp[2 * x + y] = b;
+            if (b) m.pres |= 1 << (2 * x + y);
+        }
+    return m;
+}
+
+// Decision nibble of the cell p steps back along (di, dj) from the walk's
+// cell (r0, c0) = (i - 1, j - 1): -2 at the matrix border, -3 outside the
+// window, -1 in a tile that was not recomputed.  lr0 = r0 - m.r_lo.
+template <typename Word, int R>
+__device__ __forceinline__ int window_nibble(const WalkWindow &m, const Word *win, int lr0, int c0, int di, int dj, int p) {
+    const int rr = lr0 - di * p, c = c0 - dj * p;
+    if (rr + m.r_lo < 0 || c < 0) return -2;
+    if (rr < 0) return -3;
+    const int g = rr / R;
+    const int k = c - m.chi + (m.ng - 1 - g) * R;
+    if ((unsigned)k >= (unsigned)kWinCols) return -3;
+    if (!((m.pres >> (2 * (rr >= m.lrb) + (c >= m.cb))) & 1)) return -1;
+    const Word w = win[g * kWinCols + k];
+    return (int)((unsigned long long)w >> (4 * (rr - g * R))) & 15;
 }
 
 template <typename Word, int R>
-__global__ void walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs, long long max_iters)
+__global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs,
+                                                          long long max_iters)
 {
+    static_assert(kWinRows % R == 0, "a window holds whole row groups");
+    extern __shared__ __align__(16) unsigned char walk_smem[];
+    Word *s_win = reinterpret_cast<Word *>(walk_smem);
     __shared__ const Word *s_tiles[kWalkTableMax];
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    __shared__ WalkState s_w;
+    __shared__ WalkWindow s_m;
+    __shared__ int s_stop;
+    if (blockIdx.x != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntab = T.nI * T.nJ;
-    if (ntab > kWalkTableMax) {                          // the host keeps bands smaller than this
-        if (lane == 0) st->done = 2;
+    if (ntab > kWalkTableMax || T.BT < kWalkMinBT) {     // the host keeps bands and tiles within these
+        if (threadIdx.x == 0) st->done = 2;
         return;
     }
-    for (int k = lane; k < ntab; k += 32) s_tiles[k] = T.bits[k];
-    __syncwarp();
-    WalkState w = *st;
-    auto emit = [&](int op, int cnt) {          // lane 0 only
-        if (op == w.cur_op) { w.cur_len += cnt; return; }
-        if (w.cur_len > 0) runs[w.nruns++] = make_int2(w.cur_op, w.cur_len);
-        w.cur_op = op;
-        w.cur_len = cnt;
-    };
-    long long it = 0;
-    while (w.done == 0 && ++it < max_iters) {
-        if (w.state == 0 && (w.i == 0 || w.j == 0)) { w.done = 1; break; }
-        // the next 32 * kLook cells of the run: the diagonal in state H, the row to the
-        // left in state E, the column above in state F; all loads are issued at once
-        const int di = w.state == 1 ? 0 : 1, dj = w.state == 2 ? 0 : 1;
-        const int mask = w.state == 0 ? 3 : (w.state == 1 ? 4 : 8);
-        WalkPos P;
-        P.I = (max(w.i, 1) - 1) / T.BT;
-        P.J = (max(w.j, 1) - 1) / T.BT;
-        P.li = (w.i - 1) - P.I * T.BT;
-        P.lj = (w.j - 1) - P.J * T.BT;
-        int nb[kLook];
+    for (int k = threadIdx.x; k < ntab; k += blockDim.x) s_tiles[k] = T.bits[k];
+    if (threadIdx.x == 0) { s_w = *st; s_stop = s_w.done != 0; }
+    __syncthreads();
+    long long it = 0;                                    // walk iterations (warp 0)
+    while (!s_stop) {
+        // ---- the window at the walk's cell
+        if (threadIdx.x == 0) s_m = make_window<Word, R>(T, s_tiles, s_w.i - 1, s_w.j - 1);
+        __syncthreads();
+        {
+            // thread t stages column k = t % kWinCols of every other row group, kStage
+            // independent loads in flight at a time
+            const WalkWindow m = s_m;
+            constexpr int kGroupsPerPass = kWalkThreads / kWinCols;
+            static_assert(kWalkThreads % kWinCols == 0, "whole row groups per pass");
+            const int k = threadIdx.x % kWinCols;
+            for (int g0 = threadIdx.x / kWinCols; g0 < m.ng; g0 += kStage * kGroupsPerPass) {
+                Word v[kStage];
 #pragma unroll
-        for (int q = 0; q < kLook; ++q)
-            nb[q] = nibble_back<Word, R>(T, s_tiles, P, w.i, w.j, di, dj, q * 32 + lane,
-                                         reinterpret_cast<const Word *>(st));
-        // first cell that ends the run: in H a source other than "diagonal", in E / F
-        // the opened bit; a missing tile or the border ends it too
-        int pos = 32 * kLook, nbk = 0;
+                for (int u = 0; u < kStage; ++u) {
+                    const int g = g0 + u * kGroupsPerPass;
+                    const int c = m.chi - (m.ng - 1 - g) * R + k;
+                    const int x = g * R >= m.lrb, y = c >= m.cb;
+                    const Word *b = static_cast<const Word *>(x ? (y ? m.tp[3] : m.tp[2]) : (y ? m.tp[1] : m.tp[0]));
+                    const int rb = x ? m.rbase[1] : m.rbase[0], cbs = y ? m.cbase[1] : m.cbase[0];
+                    v[u] = 0;
+                    if (g < m.ng && c >= 0 && b)      // a row group never straddles tiles (BT % R == 0)
+                        v[u] = __ldcg(b + (size_t)((m.r_lo + g * R - rb) / R) * (size_t)T.BT + (size_t)(c - cbs));
+                }
 #pragma unroll
-        for (int q = 0; q < kLook; ++q) {
-            const bool end = nb[q] < 0 || (w.state == 0 ? (nb[q] & 3) != 1 : (nb[q] & mask) != 0);
-            const unsigned ends = __ballot_sync(kFull, end);
-            if (ends) {
-                const int k = __ffs(ends) - 1;
-                pos = q * 32 + k;
-                nbk = __shfl_sync(kFull, nb[q], k);
-                break;
+                for (int u = 0; u < kStage; ++u) {
+                    const int g = g0 + u * kGroupsPerPass;
+                    if (g < m.ng) s_win[g * kWinCols + k] = v[u];
+                }
             }
         }
-        const int op = w.state;                          // M, I or D runs of states H, E, F
-        if (pos == 32 * kLook) {                         // the whole look-ahead continues the run
-            if (lane == 0) emit(op, pos);
-            w.i -= di * pos;
-            w.j -= dj * pos;
-            continue;
-        }
-        if (w.state == 0) {
-            if (lane == 0 && pos > 0) emit(0, pos);
-            w.i -= pos;
-            w.j -= pos;
-            if (nbk == -2) { w.done = 1; break; }        // reached the border
-            if (nbk == -1) break;                        // tile not computed: ask the host
-            const int src = nbk & 3;
-            if (src == 0) { w.done = 1; break; }
-            w.state = (src == 2) ? 1 : 2;
-        } else {
-            if (nbk == -1) {                             // missing tile: consume what was read
-                if (lane == 0 && pos > 0) emit(op, pos);
-                w.i -= di * pos;
-                w.j -= dj * pos;
-                break;
+        __syncthreads();
+        if (warp == 0) {
+            const WalkWindow m = s_m;
+            WalkState w = s_w;
+            auto emit = [&](int op, int cnt) {          // lane 0 only
+                if (op == w.cur_op) { w.cur_len += cnt; return; }
+                if (w.cur_len > 0) runs[w.nruns++] = make_int2(w.cur_op, w.cur_len);
+                w.cur_op = op;
+                w.cur_len = cnt;
+            };
+            bool stop = false;                           // back to the host (or finished)
+            while (true) {
+                if (w.done != 0) { stop = true; break; }
+                if (++it >= max_iters) { w.done = 2; stop = true; break; }
+                if (w.state == 0 && (w.i == 0 || w.j == 0)) { w.done = 1; stop = true; break; }
+                // the next 32 * kLook cells of the run: the diagonal in state H, the row to
+                // the left in state E, the column above in state F
+                const int di = w.state == 1 ? 0 : 1, dj = w.state == 2 ? 0 : 1;
+                const int mask = w.state == 0 ? 3 : (w.state == 1 ? 4 : 8);
+                const int lr0 = w.i - 1 - m.r_lo, c0 = w.j - 1;
+                int nb[kLook];
+#pragma unroll
+                for (int q = 0; q < kLook; ++q)
+                    nb[q] = window_nibble<Word, R>(m, s_win, lr0, c0, di, dj, q * 32 + lane);
+                // first cell that ends the run: in H a source other than "diagonal", in E / F
+                // the opened bit; the window's edge, a missing tile or the border ends it too
+                int pos = 32 * kLook, nbk = 0;
+#pragma unroll
+                for (int q = 0; q < kLook; ++q) {
+                    const bool end = nb[q] < 0 || (w.state == 0 ? (nb[q] & 3) != 1 : (nb[q] & mask) != 0);
+                    const unsigned ends = __ballot_sync(kFull, end);
+                    if (ends) {
+                        const int k = __ffs(ends) - 1;
+                        pos = q * 32 + k;
+                        nbk = __shfl_sync(kFull, nb[q], k);
+                        break;
+                    }
+                }
+                const int op = w.state;                  // M, I or D runs of states H, E, F
+                if (pos == 32 * kLook) {                 // the whole look-ahead continues the run
+                    if (lane == 0) emit(op, pos);
+                    w.i -= di * pos;
+                    w.j -= dj * pos;
+                    continue;
+                }
+                if (nbk == -3) {                         // the window's edge: take what was read
+                    if (lane == 0 && pos > 0) emit(op, pos);
+                    w.i -= di * pos;
+                    w.j -= dj * pos;
+                    break;                               // the next window starts here
+                }
+                if (w.state == 0) {
+                    if (lane == 0 && pos > 0) emit(0, pos);
+                    w.i -= pos;
+                    w.j -= pos;
+                    if (nbk == -2) { w.done = 1; stop = true; break; }   // reached the border
+                    if (nbk == -1) { stop = true; break; }              // tile not computed: ask the host
+                    const int src = nbk & 3;
+                    if (src == 0) { w.done = 1; stop = true; break; }
+                    w.state = (src == 2) ? 1 : 2;
+                } else {
+                    if (nbk == -1) {                     // missing tile: consume what was read
+                        if (lane == 0 && pos > 0) emit(op, pos);
+                        w.i -= di * pos;
+                        w.j -= dj * pos;
+                        stop = true;
+                        break;
+                    }
+                    if (nbk == -2) { w.done = 2; stop = true; break; }  // a gap cannot reach the border
+                    if (lane == 0) emit(op, pos + 1);    // the extensions and the opening cell
+                    w.i -= di * (pos + 1);
+                    w.j -= dj * (pos + 1);
+                    w.state = 0;
+                }
             }
-            if (nbk == -2) { w.done = 2; break; }        // a gap cannot reach the border
-            if (lane == 0) emit(op, pos + 1);            // the extensions and the opening cell
-            w.i -= di * (pos + 1);
-            w.j -= dj * (pos + 1);
-            w.state = 0;
+            if (lane == 0) {
+                s_w = w;
+                s_stop = stop;
+            }
         }
+        __syncthreads();
     }
-    if (w.done == 0 && it >= max_iters) w.done = 2;
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
+        WalkState w = s_w;
         if (w.done == 1 && w.cur_len > 0) {
             runs[w.nruns++] = make_int2(w.cur_op, w.cur_len);
             w.cur_len = 0;
