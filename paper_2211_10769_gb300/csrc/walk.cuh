@@ -11,13 +11,14 @@
 //   state F: emit D, go up; back to H if the F-opened bit is set.
 //
 // The walk is a chain of dependent lookups, so it reads them from shared
-// memory: the block stages a window of the decision words that follows the
-// diagonal through the walk's cell (kWinRows rows above it, kWinCols
-// columns per row group, kWinRight of them right of the diagonal), one
-// warp walks inside it, and the block stages the next window where the
-// walk left the last one.  The path of a pair worth aligning stays near a
-// diagonal, so a window holds several hundred of its cells; a long gap
-// only costs extra windows.
+// memory: a window of the decision words that follows the diagonal through
+// the walk's cell (kWinRows rows above it, kWinCols columns per row group,
+// kWinRight of them right of the diagonal).  Warp 0 walks inside one window
+// while warps 1..8 stage the next one in a second buffer: the same band
+// continued above the first, which is where a walk that follows the
+// diagonal leaves it.  Where the walk left the window elsewhere (a long
+// gap drifts it off the diagonal), the next window is staged at its cell
+// while it waits.
 //
 // One warp walks.  Runs are taken 64 cells at a time: in state H the lanes
 // read the cells of the diagonal ahead and the walk jumps over the leading
@@ -57,12 +58,14 @@ constexpr int kWalkTableMax = 4096;   // tile-table entries cached in shared mem
 constexpr int kWinRows = 768;         // rows of a window (a multiple of every R)
 constexpr int kWinCols = 128;         // columns a window keeps per row group
 constexpr int kWinRight = 64;         // ... of them right of the diagonal through the walk's cell
-constexpr int kWalkThreads = 256;     // threads staging a window (warp 0 also walks)
+constexpr int kStageThreads = 256;    // threads staging a window (warps 1..8)
+constexpr int kWalkThreads = 32 + kStageThreads;   // warp 0 walks
 constexpr int kStage = 16;            // window words a thread loads at once
+constexpr int kWinMargin = 16;        // columns a staged window must leave either side of the walk's cell
 constexpr int kWalkMinBT = 1024;      // tiles at least this side: a window meets 2 x 2 tiles at most
 
 template <int R>
-constexpr size_t walk_window_bytes(size_t word_bytes) { return (size_t)(kWinRows / R) * kWinCols * word_bytes; }
+constexpr size_t walk_window_bytes(size_t word_bytes) { return 2 * (size_t)(kWinRows / R) * kWinCols * word_bytes; }
 
 // Where a window lies (all coordinates 0-based).  Row groups g = 0 .. ng-1
 // hold rows r_lo + g*R .. r_lo + g*R + R - 1 (r_lo a multiple of R); group
@@ -86,19 +89,17 @@ __device__ __forceinline__ const Word *tile_ptr(const TileTable<Word> &T, const 
     return (ti >= 0 && tj >= 0 && ti < T.nI && tj < T.nJ) ? tiles[ti * T.nJ + tj] : nullptr;
 }
 
-// The window whose last row group holds the walk's cell (r0, c0), with that
-// cell kWinRight columns left of the group's last kept column.
+// The window whose last row group is ghi (>= 0) and keeps columns from chi
+// on in that group.
 template <typename Word, int R>
-__device__ WalkWindow make_window(const TileTable<Word> &T, const Word *const *tiles, int r0, int c0) {
+__device__ WalkWindow make_window_g(const TileTable<Word> &T, const Word *const *tiles, int ghi, int chi) {
     constexpr int RG = kWinRows / R;
     constexpr int kNone = 0x7fffffff;
     WalkWindow m;
-    r0 = max(r0, 0);
-    c0 = max(c0, 0);
-    const int ghi = r0 / R, glo = max(0, ghi - (RG - 1));
+    const int glo = max(0, ghi - (RG - 1));
     m.ng = ghi - glo + 1;
     m.r_lo = glo * R;
-    m.chi = c0 - (kWinCols - 1 - kWinRight);
+    m.chi = chi;
     const int BT = T.BT;
     const int ia = m.r_lo / BT, ib = (ghi * R + R - 1) / BT;
     m.lrb = ib > ia ? ib * BT - m.r_lo : kNone;
@@ -115,6 +116,54 @@ __device__ WalkWindow make_window(const TileTable<Word> &T, const Word *const *t
             if (b) m.pres |= 1 << (2 * x + y);
         }
     return m;
+}
+
+// The window whose last row group holds the walk's cell (r0, c0), with that
+// cell kWinRight columns left of the group's last kept column.
+template <typename Word, int R>
+__device__ WalkWindow make_window(const TileTable<Word> &T, const Word *const *tiles, int r0, int c0) {
+    r0 = max(r0, 0);
+    c0 = max(c0, 0);
+    return make_window_g<Word, R>(T, tiles, r0 / R, c0 - (kWinCols - 1 - kWinRight));
+}
+
+// Whether window m holds the cell (r0, c0) at least kWinMargin columns from
+// either side of its band.
+template <int R>
+__device__ __forceinline__ bool window_holds(const WalkWindow &m, int r0, int c0) {
+    const int rr = r0 - m.r_lo;
+    if (m.ng <= 0 || rr < 0 || rr >= m.ng * R) return false;
+    const int k = c0 - m.chi + (m.ng - 1 - rr / R) * R;
+    return k >= kWinMargin && k < kWinCols - kWinMargin;
+}
+
+// Stage window m into win: staging thread t (of kStageThreads) takes column
+// k = t % kWinCols of every kStageThreads / kWinCols-th row group, kStage
+// independent loads in flight at a time.
+template <typename Word, int R>
+__device__ __forceinline__ void stage_window(const TileTable<Word> &T, const WalkWindow &m, Word *win, int t) {
+    constexpr int kGroupsPerPass = kStageThreads / kWinCols;
+    static_assert(kStageThreads % kWinCols == 0, "whole row groups per pass");
+    const int k = t % kWinCols;
+    for (int g0 = t / kWinCols; g0 < m.ng; g0 += kStage * kGroupsPerPass) {
+        Word v[kStage];
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int g = g0 + u * kGroupsPerPass;
+            const int c = m.chi - (m.ng - 1 - g) * R + k;
+            const int x = g * R >= m.lrb, y = c >= m.cb;
+            const Word *b = static_cast<const Word *>(x ? (y ? m.tp[3] : m.tp[2]) : (y ? m.tp[1] : m.tp[0]));
+            const int rb = x ? m.rbase[1] : m.rbase[0], cbs = y ? m.cbase[1] : m.cbase[0];
+            v[u] = 0;
+            if (g < m.ng && c >= 0 && b)              // a row group never straddles tiles (BT % R == 0)
+                v[u] = __ldcg(b + (size_t)((m.r_lo + g * R - rb) / R) * (size_t)T.BT + (size_t)(c - cbs));
+        }
+#pragma unroll
+        for (int u = 0; u < kStage; ++u) {
+            const int g = g0 + u * kGroupsPerPass;
+            if (g < m.ng) win[g * kWinCols + k] = v[u];
+        }
+    }
 }
 
 // Decision nibble of the cell p steps back along (di, dj) from the walk's
@@ -138,12 +187,13 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
                                                           long long max_iters)
 {
     static_assert(kWinRows % R == 0, "a window holds whole row groups");
+    constexpr int kWinWords = (kWinRows / R) * kWinCols;
     extern __shared__ __align__(16) unsigned char walk_smem[];
-    Word *s_win = reinterpret_cast<Word *>(walk_smem);
+    Word *s_buf = reinterpret_cast<Word *>(walk_smem);   // two windows
     __shared__ const Word *s_tiles[kWalkTableMax];
     __shared__ WalkState s_w;
-    __shared__ WalkWindow s_m;
-    __shared__ int s_stop;
+    __shared__ WalkWindow s_mw[2];
+    __shared__ int s_stop, s_redo;
     if (blockIdx.x != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntab = T.nI * T.nJ;
@@ -152,43 +202,33 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
         return;
     }
     for (int k = threadIdx.x; k < ntab; k += blockDim.x) s_tiles[k] = T.bits[k];
-    if (threadIdx.x == 0) { s_w = *st; s_stop = s_w.done != 0; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_w = *st;
+        s_stop = s_w.done != 0;
+        s_mw[0] = make_window<Word, R>(T, s_tiles, s_w.i - 1, s_w.j - 1);
+    }
+    __syncthreads();
+    if (warp > 0 && !s_stop) stage_window<Word, R>(T, s_mw[0], s_buf, threadIdx.x - 32);
     __syncthreads();
     long long it = 0;                                    // walk iterations (warp 0)
+    int cur = 0;
     while (!s_stop) {
-        // ---- the window at the walk's cell
-        if (threadIdx.x == 0) s_m = make_window<Word, R>(T, s_tiles, s_w.i - 1, s_w.j - 1);
-        __syncthreads();
-        {
-            // thread t stages column k = t % kWinCols of every other row group, kStage
-            // independent loads in flight at a time
-            const WalkWindow m = s_m;
-            constexpr int kGroupsPerPass = kWalkThreads / kWinCols;
-            static_assert(kWalkThreads % kWinCols == 0, "whole row groups per pass");
-            const int k = threadIdx.x % kWinCols;
-            for (int g0 = threadIdx.x / kWinCols; g0 < m.ng; g0 += kStage * kGroupsPerPass) {
-                Word v[kStage];
-#pragma unroll
-                for (int u = 0; u < kStage; ++u) {
-                    const int g = g0 + u * kGroupsPerPass;
-                    const int c = m.chi - (m.ng - 1 - g) * R + k;
-                    const int x = g * R >= m.lrb, y = c >= m.cb;
-                    const Word *b = static_cast<const Word *>(x ? (y ? m.tp[3] : m.tp[2]) : (y ? m.tp[1] : m.tp[0]));
-                    const int rb = x ? m.rbase[1] : m.rbase[0], cbs = y ? m.cbase[1] : m.cbase[0];
-                    v[u] = 0;
-                    if (g < m.ng && c >= 0 && b)      // a row group never straddles tiles (BT % R == 0)
-                        v[u] = __ldcg(b + (size_t)((m.r_lo + g * R - rb) / R) * (size_t)T.BT + (size_t)(c - cbs));
-                }
-#pragma unroll
-                for (int u = 0; u < kStage; ++u) {
-                    const int g = g0 + u * kGroupsPerPass;
-                    if (g < m.ng) s_win[g * kWinCols + k] = v[u];
-                }
-            }
+        const int nxt = cur ^ 1;
+        if (threadIdx.x == 0) {
+            // the band continued above the current window (none above the first row)
+            const WalkWindow &m = s_mw[cur];
+            WalkWindow p;
+            if (m.r_lo > 0) p = make_window_g<Word, R>(T, s_tiles, m.r_lo / R - 1, m.chi - m.ng * R);
+            else p.ng = 0;
+            s_mw[nxt] = p;
         }
         __syncthreads();
-        if (warp == 0) {
-            const WalkWindow m = s_m;
+        if (warp > 0) {
+            if (s_mw[nxt].ng > 0) stage_window<Word, R>(T, s_mw[nxt], s_buf + nxt * kWinWords, threadIdx.x - 32);
+        } else {
+            const Word *s_win = s_buf + cur * kWinWords;
+            const WalkWindow m = s_mw[cur];
             WalkState w = s_w;
             auto emit = [&](int op, int cnt) {          // lane 0 only
                 if (op == w.cur_op) { w.cur_len += cnt; return; }
@@ -267,6 +307,18 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
             }
         }
         __syncthreads();
+        if (s_stop) break;
+        // the staged window serves if it holds the walk's cell with room to both sides
+        if (threadIdx.x == 0) {
+            s_redo = !window_holds<R>(s_mw[nxt], s_w.i - 1, s_w.j - 1);
+            if (s_redo) s_mw[nxt] = make_window<Word, R>(T, s_tiles, s_w.i - 1, s_w.j - 1);
+        }
+        __syncthreads();
+        if (s_redo) {
+            if (warp > 0) stage_window<Word, R>(T, s_mw[nxt], s_buf + nxt * kWinWords, threadIdx.x - 32);
+            __syncthreads();
+        }
+        cur = nxt;
     }
     if (threadIdx.x == 0) {
         WalkState w = s_w;
