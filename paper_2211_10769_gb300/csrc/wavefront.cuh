@@ -179,7 +179,10 @@ enum FillMode { kModeScore = 0, kModeScoreCk = 1, kModeTb = 2 };
 
 constexpr int kCH = 32;       // steps between the warps' counter updates: fewer hand-offs against
                               // more lag between warps (32 measured best of 8..64 on GB300)
-constexpr int kUnroll = 8;    // steps per unrolled body of the steady loop (4, 8, 16: 8 best)
+// Steps per unrolled body of the steady loop.  Measured on GB300 (2, 4, 8, 16): the
+// traceback fill, whose body also packs decision words, runs best at 4; the score
+// fills at 8, and at 16 when a lane holds only 4 rows (a short body).
+constexpr int fill_unroll(int R, int MODE) { return MODE == kModeTb ? 4 : (R <= 4 ? 16 : 8); }
 constexpr int kQS = 256;      // boundary-ring columns per channel
 constexpr int kQB = 1024;     // residue-ring columns
 constexpr int kIOB = 64;      // columns per I/O batch
@@ -284,7 +287,8 @@ wavefront_kernel(const FillLaunch L)
     constexpr int HC = W * 32 * R;
     constexpr int CH = kCH, QS = kQS, QB = kQB, IOB = kIOB;
     static_assert(QS >= 2 * IOB + 2 * CH + 64, "ring too small");
-    static_assert(CH % kUnroll == 0, "chunks are whole unrolled groups");
+    constexpr int UNR = fill_unroll(R, MODE);
+    static_assert(CH % UNR == 0, "chunks are whole unrolled groups");
 
     extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC scores of PB bytes
     constexpr int PB = PK == kProf32 ? 4 : 1;
@@ -512,7 +516,7 @@ wavefront_kernel(const FillLaunch L)
                 // border state (H = 0, E and F at -open, which give column 0 the same values)
                 if ((s0 >= 31 || virt_ok) && s0 + CH + 1 <= n) {
                     // steady state: every lane's column and the prefetched one are in [0, n)
-#pragma unroll kUnroll
+#pragma unroll UNR
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
                         const int cn = min((int)bring[(s + 1 - lane) & (QB - 1)], K);
@@ -531,13 +535,13 @@ wavefront_kernel(const FillLaunch L)
                     // one (lane l + 1 only reads lane l's column when it is its own); the steps
                     // need no per-lane bounds test.  Steps go in whole unrolled groups (a test
                     // inside the unrolled body would keep it from unrolling), so up to
-                    // kUnroll - 1 steps run past the last one (n + 30) and lane 31 may write
-                    // columns n .. n + kUnroll - 2 to the ring: the wait on the consumer above
+                    // UNR - 1 steps run past the last one (n + 30) and lane 31 may write
+                    // columns n .. n + UNR - 2 to the ring: the wait on the consumer above
                     // covers them.
-                    for (int g = 0; g < CH; g += kUnroll) {
+                    for (int g = 0; g < CH; g += UNR) {
                         if (s0 + g >= n + 31) break;
 #pragma unroll
-                        for (int k = 0; k < kUnroll; ++k) {
+                        for (int k = 0; k < UNR; ++k) {
                             const int s = s0 + g + k;
                             const int jn = s + 1 - lane;
                             const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
