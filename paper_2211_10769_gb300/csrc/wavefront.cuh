@@ -288,6 +288,10 @@ wavefront_kernel(const FillLaunch L)
     constexpr int CH = kCH, QS = kQS, QB = kQB, IOB = kIOB;
     static_assert(QS >= 2 * IOB + 2 * CH + 64, "ring too small");
     constexpr int UNR = fill_unroll(R, MODE);
+    // the unchecked tail below pays off where strips are few and their ends sit on the
+    // critical path; with 16-row lanes its extra unrolled body slowed the steady state of
+    // long sweeps (measured on GB300), so those keep the bounds-checked tail
+    constexpr bool kEdgeFast = R <= 12;
     static_assert(CH % UNR == 0, "chunks are whole unrolled groups");
 
     extern __shared__ __align__(16) int8_t prof[];   // (K + 1) * HC scores of PB bytes
@@ -528,7 +532,7 @@ wavefront_kernel(const FillLaunch L)
                         for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
                     }
-                } else if (virt_ok) {
+                } else if (kEdgeFast && virt_ok) {
                     // the sweep's last steps (and short sweeps): a lane right of the task reads
                     // the padding residue and lane 0 an -inf row above, so every value such a
                     // lane computes stays below the task's best cell and never reaches a real
