@@ -42,10 +42,10 @@ SM_MAX_MHZ = 2070.0
 OPS_PER_CELL = 10               # E: 2 sub + max, F: 2 sub + max, H: add + 3 max (incl. 0), running max
 WORKLOAD = "dna_pair_200kbp_align"
 # DRAM traffic of the forward fill measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, one full-size launch: 5.90 MB + 378.76 MB over
+# dram__bytes_write.sum, one full-size launch: 4.36 MB + 378.48 MB over
 # 200,000 x 200,000 cells) per cell, and the kernel source it was taken on.
-FILL_TRAFFIC = {"mode": "align", "bytes_per_cell": (5.90e6 + 378.76e6) / 4.0e10,
-                "source_sha256": "35bf99763998cbeaff6f234bcf64198e25fc8bbc11be8a760756a71241545975"}
+FILL_TRAFFIC = {"mode": "align", "bytes_per_cell": (4.36e6 + 378.48e6) / 4.0e10,
+                "source_sha256": "cadc6e19781c7db5963c3eae7c9338aae3655940d8587b8a5a1ade4af4b1f059"}
 
 
 def parse():
