@@ -230,15 +230,18 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
             const Word *s_win = s_buf + cur * kWinWords;
             const WalkWindow m = s_mw[cur];
             WalkState w = s_w;
-            auto emit = [&](int op, int cnt) {          // lane 0 only
+            // every lane keeps the same (uniform) run state; lane 0 stores the records
+            auto emit = [&](int op, int cnt) {
                 if (op == w.cur_op) { w.cur_len += cnt; return; }
-                if (w.cur_len > 0) runs[w.nruns++] = make_int2(w.cur_op, w.cur_len);
+                if (w.cur_len > 0) {
+                    if (lane == 0) runs[w.nruns] = make_int2(w.cur_op, w.cur_len);
+                    ++w.nruns;
+                }
                 w.cur_op = op;
                 w.cur_len = cnt;
             };
             bool stop = false;                           // back to the host (or finished)
-            while (true) {
-                if (w.done != 0) { stop = true; break; }
+            while (true) {                               // (w.done is 0 here: every exit that sets it breaks)
                 if (++it >= max_iters) { w.done = 2; stop = true; break; }
                 if (w.state == 0 && (w.i == 0 || w.j == 0)) { w.done = 1; stop = true; break; }
                 // the next 32 * kLook cells of the run: the diagonal in state H, the row to
@@ -251,34 +254,30 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
                 for (int q = 0; q < kLook; ++q)
                     nb[q] = window_nibble<Word, R>(m, s_win, lr0, c0, di, dj, q * 32 + lane);
                 // first cell that ends the run: in H a source other than "diagonal", in E / F
-                // the opened bit; the window's edge, a missing tile or the border ends it too
-                int pos = 32 * kLook, nbk = 0;
-#pragma unroll
-                for (int q = 0; q < kLook; ++q) {
-                    const bool end = nb[q] < 0 || (w.state == 0 ? (nb[q] & 3) != 1 : (nb[q] & mask) != 0);
-                    const unsigned ends = __ballot_sync(kFull, end);
-                    if (ends) {
-                        const int k = __ffs(ends) - 1;
-                        pos = q * 32 + k;
-                        nbk = __shfl_sync(kFull, nb[q], k);
-                        break;
-                    }
-                }
+                // the opened bit; the window's edge, a missing tile or the border ends it too.
+                // Both votes at once, one 64-bit scan, one shuffle: no loop, no divergence.
+                static_assert(kLook == 2, "the scan below reads two groups of 32 cells");
+                const bool end0 = nb[0] < 0 || (w.state == 0 ? (nb[0] & 3) != 1 : (nb[0] & mask) != 0);
+                const bool end1 = nb[1] < 0 || (w.state == 0 ? (nb[1] & 3) != 1 : (nb[1] & mask) != 0);
+                const unsigned long long ends = (unsigned long long)__ballot_sync(kFull, end0) |
+                                                ((unsigned long long)__ballot_sync(kFull, end1) << 32);
+                const int pos = ends ? __ffsll((long long)ends) - 1 : 64;
+                const int nbk = __shfl_sync(kFull, pos >= 32 ? nb[1] : nb[0], pos & 31);
                 const int op = w.state;                  // M, I or D runs of states H, E, F
-                if (pos == 32 * kLook) {                 // the whole look-ahead continues the run
-                    if (lane == 0) emit(op, pos);
+                if (pos == 64) {                         // the whole look-ahead continues the run
+                    emit(op, pos);
                     w.i -= di * pos;
                     w.j -= dj * pos;
                     continue;
                 }
                 if (nbk == -3) {                         // the window's edge: take what was read
-                    if (lane == 0 && pos > 0) emit(op, pos);
+                    if (pos > 0) emit(op, pos);
                     w.i -= di * pos;
                     w.j -= dj * pos;
                     break;                               // the next window starts here
                 }
                 if (w.state == 0) {
-                    if (lane == 0 && pos > 0) emit(0, pos);
+                    if (pos > 0) emit(0, pos);
                     w.i -= pos;
                     w.j -= pos;
                     if (nbk == -2) { w.done = 1; stop = true; break; }   // reached the border
@@ -288,14 +287,14 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
                     w.state = (src == 2) ? 1 : 2;
                 } else {
                     if (nbk == -1) {                     // missing tile: consume what was read
-                        if (lane == 0 && pos > 0) emit(op, pos);
+                        if (pos > 0) emit(op, pos);
                         w.i -= di * pos;
                         w.j -= dj * pos;
                         stop = true;
                         break;
                     }
                     if (nbk == -2) { w.done = 2; stop = true; break; }  // a gap cannot reach the border
-                    if (lane == 0) emit(op, pos + 1);    // the extensions and the opening cell
+                    emit(op, pos + 1);                   // the extensions and the opening cell
                     w.i -= di * (pos + 1);
                     w.j -= dj * (pos + 1);
                     w.state = 0;
