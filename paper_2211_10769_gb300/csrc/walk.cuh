@@ -174,7 +174,7 @@ __device__ __forceinline__ int window_nibble(const WalkWindow &m, const Word *wi
     const int rr = lr0 - di * p, c = c0 - dj * p;
     if (rr + m.r_lo < 0 || c < 0) return -2;
     if (rr < 0) return -3;
-    const int g = rr / R;
+    const int g = (int)((unsigned)rr / R);
     const int k = c - m.chi + (m.ng - 1 - g) * R;
     if ((unsigned)k >= (unsigned)kWinCols) return -3;
     if (!((m.pres >> (2 * (rr >= m.lrb) + (c >= m.cb))) & 1)) return -1;
@@ -183,7 +183,7 @@ __device__ __forceinline__ int window_nibble(const WalkWindow &m, const Word *wi
 }
 
 template <typename Word, int R>
-__global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs,
+__global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs,
                                                           long long max_iters)
 {
     static_assert(kWinRows % R == 0, "a window holds whole row groups");
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const TileTable<Word
         if (threadIdx.x == 0) {
             // the band continued above the current window (none above the first row)
             const WalkWindow &m = s_mw[cur];
-            WalkWindow p;
+            WalkWindow p{};
             if (m.r_lo > 0) p = make_window_g<Word, R>(T, s_tiles, m.r_lo / R - 1, m.chi - m.ng * R);
             else p.ng = 0;
             s_mw[nxt] = p;
