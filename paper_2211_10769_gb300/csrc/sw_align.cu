@@ -58,10 +58,10 @@ int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, i
     T.bits = reinterpret_cast<const Word *const *>(table);
     T.I0 = I0; T.J0 = J0; T.nI = nI; T.nJ = nJ; T.BT = BT; T.R = R;
     const size_t smem = walk_window_bytes<R>(sizeof(Word));
-    static bool attr_set = false;                        // per instantiation
-    if (!attr_set) {
+    static int attr_set[64] = {0};                       // per instantiation and device
+    if (c->device >= 64 || !attr_set[c->device]) {
         CU(cudaFuncSetAttribute(walk_kernel<Word, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+        if (c->device < 64) attr_set[c->device] = 1;
     }
     const int kp = kt_begin(c, SW_KT_WALK);
     walk_kernel<Word, R><<<1, kWalkThreads, smem, c->stream>>>(T, static_cast<WalkState *>(c->walk.p),
