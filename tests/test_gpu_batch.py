@@ -1,6 +1,9 @@
 """GPU parity of the batched path (sw_batch_* / sw_score_batch): one launch
 over many uneven DNA and protein pairs gives, pair by pair, the oracle's
 score and end cell; graph replay and autotuning leave results unchanged."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -103,8 +106,22 @@ def test_full_batch_workload(ctx, oracle_mod):
         assert (h.score, h.a_end, h.b_end) == (got[k].score, got[k].a_end, got[k].b_end), k
     g = np.random.default_rng(W.BASE_SEED + 12200)
     small = [k for k, (a, b, _) in enumerate(pairs) if len(a) * len(b) < 4_000_000]
-    for k in g.choice(small, size=40, replace=False):
+    check = [int(k) for k in g.choice(small, size=40, replace=False)]
+    # and the largest pairs of each alphabet (near 20,000 x 20,000, the long-query bin)
+    for si in (0, 1):
+        ks = sorted((k for k in range(len(pairs)) if pairs[k][2] == si),
+                    key=lambda k: -len(pairs[k][0]) * len(pairs[k][1]))
+        check += [k for k in ks if len(pairs[k][0]) > 1024][:3]
+    assert sum(len(pairs[k][0]) * len(pairs[k][1]) > 3e8 for k in check) >= 4
+
+    def oracle_hit(k):
         a, b, si = pairs[k]
         mat, go, ge = sc[si]
-        assert oracle_mod.sw_score(a, b, mat, go, ge) == (got[k].score, got[k].a_end, got[k].b_end)
+        return oracle_mod.sw_score(a, b, mat, go, ge)
+
+    # the oracle is a ctypes call, which releases the GIL: threads run it in parallel
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        want = list(ex.map(oracle_hit, check))
+    for k, w in zip(check, want):
+        assert w == (got[k].score, got[k].a_end, got[k].b_end), k
     plan.close()

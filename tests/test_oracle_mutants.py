@@ -99,3 +99,33 @@ def test_mutant_is_caught(name, orig, bad):
         so = O.compile_source(c, os.path.join(d, "mutant.so"))
         failed = _battery_in_child(so)
     assert failed, "planted mistake %r was not caught by any pin" % name
+
+
+# Planted mistakes in the Python top-k of the oracle (oracle.py), each run
+# against the hand-written rankings in a module built from the mutated source.
+PY_MUTANTS = [
+    ("top-k ties by descending subject", "key=lambda s: (-int(scores[s]), s)",
+     "key=lambda s: (-int(scores[s]), -s)"),
+    ("top-k ascending score", "key=lambda s: (-int(scores[s]), s)", "key=lambda s: (int(scores[s]), s)"),
+    ("top-k drops zero scores", "return [(s, int(scores[s])) for s in order[:k]]",
+     "return [(s, int(scores[s])) for s in order[:k] if scores[s] > 0]"),
+    ("top-k off by one", "for s in order[:k]]", "for s in order[:k + 1]]"),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_python_mutant_is_caught(name, orig, bad):
+    import types
+    path = os.path.join(os.path.dirname(O.SOURCE), "oracle.py")
+    src = open(path).read()
+    assert src.count(orig) == 1, name
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = path
+    sys.modules["oracle_mutant"] = mod          # dataclasses look their module up
+    try:
+        exec(compile(src.replace(orig, bad), path, "exec"), mod.__dict__)
+    finally:
+        del sys.modules["oracle_mutant"]
+    with pytest.raises(AssertionError):
+        pins.check_top_k(mod.top_k)
+    pins.check_top_k(O.top_k)            # the real one passes

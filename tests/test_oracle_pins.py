@@ -255,3 +255,29 @@ def test_global_score_closed_forms(oracle_mod):
     loc = oracle_mod.sw_align(a, b, S, 5, 2)
     if (loc.a_begin, loc.b_begin, loc.a_end, loc.b_end) == (0, 0, len(a), len(b)):
         assert oracle_mod.nw_score(a, b, S, 5, 2) == loc.score
+
+
+# Hand-written expected rankings for the database top-k (score descending,
+# then subject index ascending; subjects scoring 0 are still ranked).  Each
+# case: (scores, k, expected [(subject, score), ...]).
+TOP_K_CASES = [
+    ([5, 9, 1, 9, 7], 3, [(1, 9), (3, 9), (4, 7)]),              # tie on score: lower subject first
+    ([3, 3, 3, 3], 4, [(0, 3), (1, 3), (2, 3), (3, 3)]),          # all tied
+    ([0, 0, 0], 2, [(0, 0), (1, 0)]),                             # all-zero scores are still ranked
+    ([4, 0, 2], 10, [(0, 4), (2, 2), (1, 0)]),                    # k > n: every subject, in order
+    ([8, 1], 0, []),                                              # k = 0
+    ([], 5, []),                                                  # empty database
+    ([1, 2, 3, 4, 5, 6], 6, [(5, 6), (4, 5), (3, 4), (2, 3), (1, 2), (0, 1)]),   # strictly ascending input
+    ([2, 10, 0, 10, 2, 7], 5, [(1, 10), (3, 10), (5, 7), (0, 2), (4, 2)]),        # two tie groups
+]
+
+
+def check_top_k(top_k):
+    """Pins a top-k function against the hand-written rankings above."""
+    for scores, k, want in TOP_K_CASES:
+        got = [(int(s), int(v)) for s, v in top_k(np.asarray(scores, dtype=np.int64), k)]
+        assert got == want, (scores, k, got, want)
+
+
+def test_top_k_hand_written_rankings(oracle_mod):
+    check_top_k(oracle_mod.top_k)
