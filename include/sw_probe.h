@@ -33,6 +33,14 @@ extern "C" {
  */
 int sw_probe_int_rate(sw_ctx *ctx, int op, int iters, double *per_sm_per_clk, double *sm_mhz);
 
+/*
+ * Latency of `op`: one warp runs one chain of iters x 32 instructions, each
+ * needing the previous one's result; writes SM clocks per instruction
+ * (the shuffle probe adds one integer add per step).  Synchronous on the
+ * context's stream.  iters >= 1.
+ */
+int sw_probe_latency(sw_ctx *ctx, int op, int iters, double *cycles_per_op);
+
 #ifdef __cplusplus
 }
 #endif

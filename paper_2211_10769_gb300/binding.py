@@ -440,3 +440,17 @@ def probe_int_rates(ctx: Context, iters: int = 2000) -> dict:
         mhz.append(f.value)
     out["sm_mhz"] = round(sum(mhz) / len(mhz), 1)
     return out
+
+
+def probe_latencies(ctx: Context, iters: int = 2000) -> dict:
+    """SM clocks from one instruction of each form to the next that needs its
+    result (sw_probe_latency: one warp, one dependent chain)."""
+    lib = load()
+    fn = lib.sw_probe_latency
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, op in PROBE_OPS.items():
+        r = ctypes.c_double()
+        _check(fn(ctx.handle, op, iters, ctypes.byref(r)), "sw_probe_latency")
+        out[name] = round(r.value, 2)
+    return out

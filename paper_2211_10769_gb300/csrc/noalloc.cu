@@ -131,7 +131,7 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     validate_codes_kernel<<<(unsigned)std::min<long long>((n + threads - 1) / threads, 4LL * nsm), threads, 0, st>>>(b, n, ds.K, err);
     CU(cudaGetLastError());
 
-    FillLaunch L;
+    FillLaunch L{};
     L.tasks = task; L.scorings = scoring; L.ticket = ticket; L.prog = prog; L.cand = cand;
     L.err = err; L.total = nstrips; L.spin_limit = 1LL << 26; L.ntasks = 1;
     const size_t smem = (size_t)(ds.K + 1) * kHC;

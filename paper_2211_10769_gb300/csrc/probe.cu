@@ -2,7 +2,10 @@
 // of the integer-ALU roofline): each probe kernel runs eight independent
 // dependency chains of one instruction form per thread on every SM and
 // reports warp-lane results per SM per clock, using the SM clock counter
-// and the global nanosecond timer read inside the kernel.
+// and the global nanosecond timer read inside the kernel.  A second probe
+// runs one dependent chain in one warp and reports the latency of a form
+// (SM clocks from one instruction to the next that needs its result), which
+// bounds a wavefront step whose rows form such a chain.
 #include "sw_probe.h"
 #include "sw_ctx.h"
 
@@ -79,7 +82,62 @@ int run(sw_ctx *c, int iters, double *per_sm_clk, double *mhz) {
     return SW_OK;
 }
 
+// One warp, one dependency chain: every instruction needs the previous
+// one's result, so the SM clock ticks per instruction are its latency.
+template <int OP>
+__global__ void __launch_bounds__(32) latency_kernel(unsigned seed, int iters, unsigned *sink,
+                                                      unsigned long long *clk)
+{
+    unsigned x = seed * (threadIdx.x + 1);
+    const unsigned y = seed ^ 0x5bd1e995u, z = seed + 0x3c6ef372u, c = seed | 1u;
+    __syncwarp();
+    const unsigned long long c0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            if constexpr (OP == SW_PROBE_SHFL) x = __shfl_xor_sync(0xffffffffu, x, 1) + 1u;
+            else x = step<OP>(x, y, z, c);
+        }
+    }
+    __syncwarp();
+    const unsigned long long c1 = clock64();
+    if (x == 0x12345678u) sink[threadIdx.x] = x;          // keeps the chain live
+    if (threadIdx.x == 0) clk[0] = c1 - c0;
+}
+
+template <int OP>
+int run_latency(sw_ctx *c, int iters, double *cycles) {
+    swgb::DevBuf buf;
+    if (buf.ensure(4096)) return SW_ENOMEM;
+    if (cudaMemsetAsync(buf.p, 0, 4096, c->stream) != cudaSuccess) return SW_ECUDA;
+    unsigned long long *clk = reinterpret_cast<unsigned long long *>(static_cast<char *>(buf.p) + 2048);
+    latency_kernel<OP><<<1, 32, 0, c->stream>>>(0x1234567u, iters, static_cast<unsigned *>(buf.p), clk);
+    if (cudaGetLastError() != cudaSuccess) return SW_ECUDA;
+    ++c->launches;
+    unsigned long long h = 0;
+    if (cudaMemcpyAsync(&h, clk, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return SW_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SW_ECUDA;
+    *cycles = (double)h / ((double)iters * 32.0);
+    return SW_OK;
+}
+
 }  // namespace
+
+extern "C" int sw_probe_latency(sw_ctx *c, int op, int iters, double *cycles) {
+    if (!c || !cycles || iters < 1) return SW_EINVAL;
+    swgb::DeviceGuard g(c->device);
+    switch (op) {
+        case SW_PROBE_IADD: return run_latency<SW_PROBE_IADD>(c, iters, cycles);
+        case SW_PROBE_IMAX: return run_latency<SW_PROBE_IMAX>(c, iters, cycles);
+        case SW_PROBE_VIADDMAX_S32: return run_latency<SW_PROBE_VIADDMAX_S32>(c, iters, cycles);
+        case SW_PROBE_VIMAX3_S32_RELU: return run_latency<SW_PROBE_VIMAX3_S32_RELU>(c, iters, cycles);
+        case SW_PROBE_VIADDMAX_S16X2: return run_latency<SW_PROBE_VIADDMAX_S16X2>(c, iters, cycles);
+        case SW_PROBE_VIMAX3_S16X2_RELU: return run_latency<SW_PROBE_VIMAX3_S16X2_RELU>(c, iters, cycles);
+        case SW_PROBE_PRMT: return run_latency<SW_PROBE_PRMT>(c, iters, cycles);
+        case SW_PROBE_SHFL: return run_latency<SW_PROBE_SHFL>(c, iters, cycles);
+        default: return SW_EINVAL;
+    }
+}
 
 extern "C" int sw_probe_int_rate(sw_ctx *c, int op, int iters, double *per_sm_per_clk, double *sm_mhz) {
     if (!c || !per_sm_per_clk || !sm_mhz || iters < 1) return SW_EINVAL;

@@ -250,6 +250,28 @@ FillConfig swgb::pair_fill_config(const sw_ctx *c, int64_t rows) {
     return FillConfig{16, 4, 0, 2};
 }
 
+// Tile shape of a single-pair fill with scoring s: the packed 16-bit fill
+// (two cells per lane operation) where it is exact for the shape, with the
+// fewest rows per lane in {8, 12, 16} that give at most one strip per SM;
+// else the int32 fill of pair_fill_config.
+FillConfig swgb::pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevScoring &s) {
+    if (!c->fwd_auto) {
+        FillConfig f = c->fwd;
+        f.P16 = f.P16 && p16_fits(s, f.R) && f.W == 4;
+        return f;
+    }
+    if (c->p16) {
+        for (int R : {8, 12, 16}) {
+            const int64_t sh = 4LL * 32 * R;
+            if ((rows + sh - 1) / sh <= (int64_t)c->nsm || R == 16) {
+                if (p16_fits(s, R)) return FillConfig{R, 4, 0, 2, 1};
+                break;
+            }
+        }
+    }
+    return pair_fill_config(c, rows);
+}
+
 // Compute warps per strip for a fill of one pair with `rows` rows.  The strips
 // of a pair form a chain (each waits on the bottom row of the one above), so
 // the chain runs at the pace of its slowest strip: two strips sharing an SM
@@ -274,6 +296,7 @@ bool swgb::fold_open(const DevScoring &s) {
 int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                       long long tickets) {
     if (tickets <= 0) return SW_OK;
+    if (cfg.P16) return launch_fill16(c, cfg, mode, L, K, tickets);
     if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets, cfg.B);
@@ -296,7 +319,7 @@ int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
     CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, tbytes, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->prog.p, 0, (size_t)tickets * sizeof(int), c->stream));
     CU(cudaMemsetAsync(c->ticket.p, 0, sizeof(unsigned long long), c->stream));
-    FillLaunch L;
+    FillLaunch L{};
     L.tasks = static_cast<const FillTask *>(c->tasks.p);
     L.scorings = static_cast<const DevScoring *>(c->scorings.p);
     L.ticket = static_cast<unsigned long long *>(c->ticket.p);
@@ -306,6 +329,7 @@ int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
     L.total = tickets;
     L.spin_limit = c->spin_limit;
     L.ntasks = (int)tasks.size();
+    L.pace_permille = c->pace_permille;
     // c->stage is pinned and copied asynchronously: callers synchronise the
     // stream before they run another fill (every ABI call ends with a sync).
     return launch_fill(c, cfg, mode, fold, L, K, tickets);
@@ -391,12 +415,14 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     c->bat = FillConfig{8, 4};
     // tuning overrides: SWGB_FWD="R,W[,S[,B]]", SWGB_TB="R,W" and SWGB_BATCH="R,W" (tile shapes of the fills)
     if (const char *f = std::getenv("SWGB_FWD")) {
-        std::sscanf(f, "%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B);
+        std::sscanf(f, "%d,%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B, &c->fwd.P16);
         c->fwd_auto = false;
     }
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
     if (const char *f = std::getenv("SWGB_PROF32")) c->prof32 = std::atoi(f) != 0;
+    if (const char *f = std::getenv("SWGB_P16")) c->p16 = std::atoi(f) != 0;
+    if (const char *f = std::getenv("SWGB_PACE")) c->pace_permille = std::max(0, std::atoi(f));
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
     if (const char *f = std::getenv("SWGB_TB_SW")) c->tb_strip_warps = std::atoi(f);
     // checkpoint memory of sw_align: 40% of the device memory free now (at least 4 GB), so that
@@ -478,7 +504,7 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
 
-    const FillConfig fwd = pair_fill_config(c, m);
+    const FillConfig fwd = pair_fill_config_for(c, m, ds);
     const int sw = pair_strip_warps(c, fwd, m);
     const int SH = sw * 32 * fwd.R;
     FillTask t{};

@@ -107,12 +107,16 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     // tiles are BT x BT; BT is a multiple of both fills' strip heights, so
     // checkpoint rows fall on forward-strip bottoms and tiles hold whole
     // traceback strips
-    const FillConfig fwd = pair_fill_config(c, m);
+    const FillConfig fwd = pair_fill_config_for(c, m, ds);
     const int sw = pair_strip_warps(c, fwd, m);
     const int HC = sw * 32 * fwd.R;
     // the traceback tiles continue the forward fill's staircase checkpoint columns lane by
     // lane, so both fills must give each lane the same rows (R)
-    const FillConfig tbc = c->tbc.R == fwd.R ? c->tbc : FillConfig{fwd.R, 4};
+    FillConfig tbc = c->tbc.R == fwd.R ? c->tbc : FillConfig{fwd.R, 4};
+    tbc.P16 = 0;                                  // traceback bits come from the int32 fill
+    // the packed forward fill stores its checkpoint columns with two positions per lane and
+    // one auxiliary record per half-group of R/2 rows
+    const int aux_rows = fwd.P16 ? fwd.R / 2 : fwd.R;
     const int HT = fill_rows_per_strip(tbc);
     const long long BL = std::lcm((long long)HC, (long long)HT);
     long long BT = BL * ((1024 + BL - 1) / BL);
@@ -140,7 +144,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     t.colck_every = (int32_t)BT;
     t.colck_ld = (long long)t.nstrips * HC;     // rows padded to whole strips (the padding is written)
     RC(c->colck.ensure((size_t)ncolck * (size_t)t.colck_ld * sizeof(int2)));
-    RC(c->colaux.ensure((size_t)ncolck * (size_t)(t.colck_ld / fwd.R) * sizeof(int2)));
+    RC(c->colaux.ensure((size_t)ncolck * (size_t)(t.colck_ld / aux_rows) * sizeof(int2)));
     t.colck = static_cast<int2 *>(c->colck.p);
     t.colck_aux = static_cast<int2 *>(c->colaux.p);
     RC(run_fill(c, fwd, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
@@ -186,7 +190,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
     RC(c->misc.ensure(table_cap * sizeof(void *)));
     const int2 *rowck = t.ckpt, *colck = t.colck, *colaux = t.colck_aux;
-    const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / fwd.R;
+    const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / aux_rows;
     int prev_i = -1, prev_j = -1, prev_state = -1;
     while (true) {
         const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
@@ -211,7 +215,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.ticket0 = tickets;
                 u.top = ti > 0 ? rowck + (size_t)(ti - 1) * n + c0 : nullptr;
                 u.left = tj > 0 ? colck + (size_t)(tj - 1) * colck_ld + r0 : nullptr;
-                u.left_aux = tj > 0 ? colaux + (size_t)(tj - 1) * colaux_ld + r0 / fwd.R : nullptr;
+                u.left_aux = tj > 0 ? colaux + (size_t)(tj - 1) * colaux_ld + r0 / aux_rows : nullptr;
+                u.left_split = fwd.P16 ? 1 : 0;
                 const size_t k = tasks.size();
                 u.nslot = std::min(u.nstrips, 2);
                 u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;

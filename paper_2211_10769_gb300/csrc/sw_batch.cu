@@ -199,7 +199,7 @@ int enqueue_run(sw_batch *B) {
             if (cudaStreamWaitEvent(bs, B->bevents[0], 0) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; break; }
             if (bin.nt > 0) {
                 const DevScoring &sc = B->scorings[(size_t)bin.sidx];
-                FillLaunch L;
+                FillLaunch L{};
                 L.tasks = static_cast<const FillTask *>(B->tasks.p) + bin.t0;
                 L.scorings = static_cast<const DevScoring *>(B->meta.p);
                 L.ticket = ctr + k;
@@ -218,7 +218,7 @@ int enqueue_run(sw_batch *B) {
         }
         c->stream = saved;
         RC(rc);
-        FillLaunch L;
+        FillLaunch L{};
         L.tasks = static_cast<const FillTask *>(B->tasks.p);
         L.cand = static_cast<int4 *>(B->cand.p);
         reduce_candidates_kernel<<<(B->ntasks + 7) / 8, 256, 0, st>>>(L.tasks, B->ntasks, L.cand,

@@ -44,6 +44,7 @@ struct FillConfig {
     int W;
     int S = 0;
     int B = 0;
+    int P16 = 0;   // packed 16-bit fill (wavefront16.cuh) instead of the int32 one
 };
 
 // Device time per kernel kind (sw_ctx_timing): event pairs recorded around
@@ -72,6 +73,8 @@ struct sw_ctx {
     swgb::FillConfig tbc{8, 4};       // traceback recompute
     swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
     bool prof32 = true;               // int32 query profiles where they fit (small alphabets)
+    bool p16 = true;                  // packed 16-bit pair fill where it is exact (p16_fits)
+    int pace_permille = 20;           // slow-down of a strip chain's first warp (FillLaunch)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
     int tb_strip_warps = 0;           // compute warps per traceback strip (0 = all)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
@@ -93,6 +96,9 @@ int map_kernel_error(int e);
 int fill_rows_per_strip(const FillConfig &cfg);
 int pair_strip_warps(const sw_ctx *c, const FillConfig &cfg, int64_t rows);
 FillConfig pair_fill_config(const sw_ctx *c, int64_t rows);
+FillConfig pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevScoring &s);   // picks P16 where exact
+bool p16_fits(const DevScoring &s, int R);
+int launch_fill16(sw_ctx *c, const FillConfig &cfg, int mode, const FillLaunch &L, int K, long long tickets);
 int tb_word_bytes(int R);
 bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
 int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,

@@ -80,6 +80,10 @@ struct FillTask {
     int64_t tb_ld;
     int32_t strip_warps;   // compute warps per strip (rows per strip = strip_warps * 32 * R);
                            // 0 = all W warps of the block
+    int32_t left_split;    // left / left_aux in the two-positions-per-lane form of the packed
+                           // fill (wavefront16.cuh): the first R/2 rows of lane l sit at column
+                           // c - 2l, the other R/2 at c - 2l - 1, and left_aux holds one record
+                           // per half-group of R/2 rows (first the top half's, then the bottom's)
 };
 
 struct FillLaunch {
@@ -92,6 +96,7 @@ struct FillLaunch {
     long long total;              // total tickets
     long long spin_limit;         // polls before a wait gives up
     int ntasks;
+    int pace_permille;            // slow-down of a long strip chain's first warp (0 = none)
 };
 
 template <int R> struct TbWord;
@@ -170,7 +175,9 @@ __device__ __forceinline__ bool warp_wait_geq(const int *ctr, int want, const vo
     while (lds_acquire(ctr) < want) {
         if (*abort_flag) return false;
         if (++it > limit) { atomicCAS(err, 0, kErrTimeout); return false; }
+#ifndef SWGB_WAIT_SPIN
         if (it > 64) __nanosleep(20);              // spin first: the producer is usually a step away
+#endif
     }
     return true;
 }
@@ -280,6 +287,199 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     }
 }
 
+// Rows [r0, r1) of one lane advanced by one column (the Gotoh update of
+// column_update restricted to a range of the lane's rows), entered with the
+// row above's H - open and F at this column; udiag = H - open of the row
+// above at the previous column.  Returns the last row's F in *fout.
+template <int R, int PK>
+__device__ __forceinline__ void rows_update(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int r0,
+                                            int r1, int uup, int fup, int udiag, int go, int ge, int *fout)
+{
+    int f = __viaddmax_s32(fup, -ge, uup);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < r0 || r >= r1) continue;
+        int sp = score_at<PK>(pw, r);
+        if constexpr (PK == kProf8) sp += go;
+        const int uold = st.U[r];
+        const int e = __viaddmax_s32(st.E[r], -ge, uold);
+        const int x = __viaddmax_s32_relu(udiag, sp, e);
+        const int xgo = x - go;
+        st.U[r] = __viaddmax_s32(f, -go, xgo);
+        st.E[r] = e;
+        udiag = uold;
+        if (r + 1 < r1) f = __viaddmax_s32(f, -ge, xgo);
+    }
+    *fout = f;
+}
+
+// A task entered from a checkpoint column written by the packed fill, whose
+// lanes hold two wavefront positions each: lane l's top half (rows
+// [0, R/2)) sits at column c - 2l, its bottom half at c - 2l - 1, where c is
+// the column left of the task.  Position v = 2l (top) or 2l + 1 (bottom)
+// advances v columns, in step with its neighbours -- the top half's k-th
+// column needs lane l-1's bottom half after its (k-1)-th, the bottom half's
+// needs this lane's top half after its (k-1)-th -- so that every row ends at
+// column c: a 63-step wavefront inside the warp.  Leaves st as the straight
+// boundary column the sweep starts from (U, E per row; ub / fb the last
+// row's H - open and F at c; udiag0 the row above at c for lane 0).
+template <int R, int W, int PK>
+__device__ __forceinline__ void split_staircase_prologue(const FillTask &T, LaneState<R> &st, const int8_t *prow,
+                                                         int grow, int lane, int K, int go, int ge)
+{
+    constexpr int H = R / 2;
+    constexpr int HC = W * 32 * R;
+    constexpr size_t PB = PK == kProf32 ? 4 : 1;
+    constexpr int NPW = ProfWords<R, PK>::N;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (grow + r < T.rows) { const int2 v = __ldcg(T.left + grow + r); st.U[r] = v.x; st.E[r] = v.y; }
+    const bool in = grow < T.rows;
+    const int2 at = in ? __ldcg(T.left_aux + grow / H) : make_int2(-go, kNeg);       // top half
+    const int2 ab = in ? __ldcg(T.left_aux + grow / H + 1) : make_int2(-go, kNeg);   // bottom half
+    int udT = at.x, fT = at.y;        // row above the top half at its column; F of its last row
+    int udB = ab.x, fB = ab.y;        // the same for the bottom half
+    for (int k = 1; k < 64; ++k) {
+        // lane l-1's bottom half after its (k-1)-th column: the row above this lane's top half
+        const int uupT = __shfl_up_sync(kFull, st.U[R - 1], 1);
+        const int fupT = __shfl_up_sync(kFull, fB, 1);
+        // the bottom half moves first: its row above is the top half before this step
+        if (k <= 2 * lane + 1) {
+            const int cb = min((int)T.b[k - 2 * lane - 2], K);   // column c - 2l - 1 + k
+            uint32_t pwk[NPW];
+            load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
+            const int uup = st.U[H - 1];
+            rows_update<R, PK>(st, pwk, H, R, uup, fT, udB, go, ge, &fB);
+            udB = uup;
+        }
+        if (k <= 2 * lane) {
+            const int cb = min((int)T.b[k - 2 * lane - 1], K);   // column c - 2l + k
+            uint32_t pwk[NPW];
+            load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
+            rows_update<R, PK>(st, pwk, 0, H, uupT, fupT, udT, go, ge, &fT);
+            udT = uupT;
+        }
+    }
+    st.ub = st.U[R - 1];
+    st.fb = fB;
+    // the diagonal of the task's first column: the row above at column c
+    const int up = __shfl_up_sync(kFull, st.ub, 1);
+    st.udiag0 = lane > 0 ? up : udT;
+}
+
+// Input warp of a fill block: streams the strip's top boundary row (the
+// matrix border, the task's top row or the previous strip's bottom row, as
+// (H - open, F), multiplied by 2^SHIFT) into channel 0 of the boundary ring and the column residues
+// into the residue ring, ahead of the first compute warp.  Room in channel 0
+// is bounded by what warp 0 consumed, room in the residue ring by what the
+// last active warp (whose lanes read furthest back, `lag` columns behind its
+// published count) has published.
+template <int QS, int QB, int IOB, int SHIFT = 0>
+__device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
+                                                int n, int go, int K, int Wa, int lag, int2 *ring0,
+                                                uint8_t *bring, int *prod, const int *cons,
+                                                volatile int *s_abort, int lane)
+{
+    int in_next = 0;
+    long long idle = 0;
+    const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
+    const int *pprev = L.prog + (tk - 1);
+    int avail_prev = strip == 0 ? n : 0;
+    while (in_next < n) {
+        const int room0 = lds_acquire(&cons[0]) + QS;
+        const int roomb = lds_acquire(&prod[Wa]) + QB - lag;
+        int target = min(n, min(in_next + IOB, min(room0, roomb)));
+        if (target > in_next && strip > 0 && avail_prev < target)
+            avail_prev = ld_acquire(pprev);              // every lane: acquire for its own loads
+        target = min(target, avail_prev);
+        if (target > in_next) {
+            for (int col = in_next + lane; col < target; col += 32) {
+                const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
+                if constexpr (SHIFT == 0)
+                    ring0[col & (QS - 1)] = make_int2(v.x - go, v.y);
+                else     // scaled values; -infinity stays far below every real value, without overflow
+                    ring0[col & (QS - 1)] = make_int2((v.x - go) * (1 << SHIFT), max(v.y, kNeg >> SHIFT) * (1 << SHIFT));
+                bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
+            }
+            __syncwarp();
+            if (lane == 0) sts_release(&prod[0], target);
+            in_next = target;
+            idle = 0;
+        } else {
+            if (*s_abort) break;
+            if (++idle > L.spin_limit) {
+                if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
+                *s_abort = 1;
+                break;
+            }
+            // far ahead of warp 0 (more than two batches buffered): poll rarely, so that the
+            // compute warp sharing this SM sub-partition keeps its issue slots
+#ifndef SWGB_INPUT_EAGER
+            if (in_next - lds_acquire(&cons[0]) > 2 * IOB) __nanosleep(256);
+            else
+#endif
+#ifndef SWGB_IO_SPIN
+            if (idle > 32) __nanosleep(32);
+#else
+            { }
+#endif
+        }
+    }
+}
+
+// Output warp of a fill block: drains the strip's bottom row (H - open, F),
+// multiplied by 2^SHIFT, from the last active warp's channel to global memory as (H, F) -- the next
+// strip's input and, every ckpt_every-th strip, a checkpoint row -- and
+// publishes the stored column count with a release store.
+template <int QS, int SHIFT = 0>
+__device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
+                                                 int n, int go, int SH, int Wa, const int2 *ringW,
+                                                 const int *prod, int *cons, volatile int *s_abort, int lane)
+{
+    int out_next = 0;
+    long long idle = 0;
+    // a checkpoint row only where the strip's bottom row lies inside the task
+    // (the last strip may be partial)
+    const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
+                    (long long)(strip + 1) * SH <= (long long)T.rows;
+    int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
+    // the last strip's bottom row feeds no other strip
+    const bool store = strip + 1 < T.nstrips;
+    int2 *dst = store ? T.bnd + (size_t)(strip % T.nslot) * n : nullptr;
+    while (out_next < n) {
+        const int avail_out = lds_acquire(&prod[Wa]);
+        if (avail_out > out_next) {
+            if (store || ck) {
+                for (int col = out_next + lane; col < avail_out; col += 32) {
+                    const int2 u = ringW[col & (QS - 1)];
+                    const int2 v = make_int2((u.x >> SHIFT) + go, u.y >> SHIFT);
+                    if (store) dst[col] = v;
+                    if (ck) cdst[col] = v;
+                }
+            }
+            // the lanes' stores are ordered before lane 0's release by the warp
+            // barrier; the release (gpu scope) publishes them cumulatively
+            __syncwarp();
+            if (lane == 0) {
+                if (store) st_release(L.prog + tk, avail_out);
+                sts_release(&cons[Wa], avail_out);
+            }
+            out_next = avail_out;
+            idle = 0;
+        } else {
+            if (*s_abort) break;
+            if (++idle > L.spin_limit) {
+                if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
+                *s_abort = 1;
+                break;
+            }
+#ifndef SWGB_IO_SPIN
+            if (idle > 32) __nanosleep(32);
+#endif
+        }
+    }
+}
+
 template <int R, int W, int MODE, int PK>
 __global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 12 ? 128 : (W > 4 ? 96 : 104))
 wavefront_kernel(const FillLaunch L)
@@ -359,82 +559,11 @@ wavefront_kernel(const FillLaunch L)
 
         if (warp == W) {
             // ================= input warp: top boundary row and residues =================
-            int in_next = 0;
-            long long idle = 0;
-            const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
-            const int *pprev = L.prog + (tk - 1);
-            int avail_prev = strip == 0 ? n : 0;
-            while (in_next < n) {
-                // room in channel 0 (consumer: warp 0) and in the residue ring
-                // (slowest reader: warp Wa-1, whose lane 31 is at column prod[Wa])
-                const int room0 = lds_acquire(&cons[0]) + QS;
-                const int roomb = lds_acquire(&prod[Wa]) + QB - 64;
-                int target = min(n, min(in_next + IOB, min(room0, roomb)));
-                if (target > in_next && strip > 0 && avail_prev < target)
-                    avail_prev = ld_acquire(pprev);              // every lane: acquire for its own loads
-                target = min(target, avail_prev);
-                if (target > in_next) {
-                    for (int col = in_next + lane; col < target; col += 32) {
-                        const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
-                        ring[0][col & (QS - 1)] = make_int2(v.x - go, v.y);
-                        bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
-                    }
-                    __syncwarp();
-                    if (lane == 0) sts_release(&prod[0], target);
-                    in_next = target;
-                    idle = 0;
-                } else {
-                    if (s_abort) break;
-                    if (++idle > L.spin_limit) {
-                        if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                    if (idle > 32) __nanosleep(32);
-                }
-            }
+            fill_input_warp<QS, QB, IOB>(T, L, strip, tk, n, go, K, Wa, 64, ring[0], bring, prod, cons,
+                                         &s_abort, lane);
         } else if (warp == W + 1) {
             // ================= output warp: bottom row to global memory =================
-            int out_next = 0;
-            long long idle = 0;
-            // a checkpoint row only where the strip's bottom row lies inside the task
-            // (the last strip may be partial)
-            const bool ck = T.ckpt_every > 0 && ((strip + 1) % T.ckpt_every) == 0 &&
-                            (long long)(strip + 1) * SH <= (long long)T.rows;
-            int2 *cdst = ck ? T.ckpt + (size_t)((strip + 1) / T.ckpt_every - 1) * n : nullptr;
-            // the last strip's bottom row feeds no other strip
-            const bool store = strip + 1 < T.nstrips;
-            int2 *dst = store ? T.bnd + (size_t)(strip % T.nslot) * n : nullptr;
-            while (out_next < n) {
-                const int avail_out = lds_acquire(&prod[Wa]);
-                if (avail_out > out_next) {
-                    if (store || ck) {
-                        for (int col = out_next + lane; col < avail_out; col += 32) {
-                            const int2 u = ring[Wa][col & (QS - 1)];
-                            const int2 v = make_int2(u.x + go, u.y);
-                            if (store) dst[col] = v;
-                            if (ck) cdst[col] = v;
-                        }
-                    }
-                    // the lanes' stores are ordered before lane 0's release by the warp
-                    // barrier; the release (gpu scope) publishes them cumulatively
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (store) st_release(L.prog + tk, avail_out);
-                        sts_release(&cons[Wa], avail_out);
-                    }
-                    out_next = avail_out;
-                    idle = 0;
-                } else {
-                    if (s_abort) break;
-                    if (++idle > L.spin_limit) {
-                        if (lane == 0) atomicCAS(L.err, 0, kErrTimeout);
-                        s_abort = 1;
-                        break;
-                    }
-                    if (idle > 32) __nanosleep(32);
-                }
-            }
+            fill_output_warp<QS>(T, L, strip, tk, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
         } else if (warp >= Wa) {
             if constexpr (MODE != kModeTb)
                 if (lane == 0) s_cand[warp] = make_int4(0, 0x7fffffff, 0x7fffffff, 0);
@@ -450,7 +579,9 @@ wavefront_kernel(const FillLaunch L)
             st.udiag0 = -go;                                // matrix border: H = 0
             st.ub = st.U[R - 1];
             st.fb = kNeg;
-            if (T.left) {
+            if (T.left && T.left_split) {
+                split_staircase_prologue<R, W, PK>(T, st, prow, grow, lane, K, go, ge);
+            } else if (T.left) {
                 // Staircase left boundary: lane l's rows hold column c - l (c = the column
                 // left of the task).  Lane l advances l columns, in step with its neighbours
                 // (lane l's k-th column needs lane l-1's (k-1)-th), so that every lane ends at

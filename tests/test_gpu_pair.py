@@ -17,17 +17,41 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["packed16", "int32"])
+def ctx(request):
+    """A context on the packed 16-bit pair fill (the default where it is
+    exact) and one restricted to the int32 fill: every test runs on both."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
-    c = binding.Context(0)
+    old = os.environ.get("SWGB_P16")
+    os.environ["SWGB_P16"] = "1" if request.param == "packed16" else "0"
+    try:
+        c = binding.Context(0)
+    finally:
+        if old is None:
+            del os.environ["SWGB_P16"]
+        else:
+            os.environ["SWGB_P16"] = old
     yield c
     c.close()
 
 
+_ORACLE_SCORES = {}
+
+
+def _oracle_score(oracle_mod, a, b, S, o, e):
+    """The oracle's score and end cell, computed once per input (both fills reuse it)."""
+    import hashlib
+    key = (hashlib.sha1(np.ascontiguousarray(a).tobytes()).hexdigest(),
+           hashlib.sha1(np.ascontiguousarray(b).tobytes()).hexdigest(),
+           np.asarray(S, np.int8).tobytes(), o, e)
+    if key not in _ORACLE_SCORES:
+        _ORACLE_SCORES[key] = oracle_mod.sw_score(a, b, S, o, e)
+    return _ORACLE_SCORES[key]
+
+
 def _score_case(ctx, oracle_mod, a, b, S, o, e):
-    want = oracle_mod.sw_score(a, b, S, o, e)
+    want = _oracle_score(oracle_mod, a, b, S, o, e)
     got = ctx.score(a, b, S, o, e)
     assert (got.score, got.a_end, got.b_end) == want, (len(a), len(b), o, e)
 
@@ -85,6 +109,45 @@ def test_score_ties_and_degenerate(ctx, oracle_mod):
     _score_case(ctx, oracle_mod, mism, mism + 1, sc.matrix, sc.gap_open, sc.gap_extend)   # score 0
     zero_gap = np.ones((4, 4), np.int8)
     _score_case(ctx, oracle_mod, runs[:300], alt[:400], zero_gap, 0, 0)
+
+
+def test_score_row_ties_inside_lane_halves(ctx, oracle_mod):
+    """Equal maxima in several rows of one column, in several columns of one
+    row, and periodic repeats that put equal maxima two or three rows apart:
+    the end cell is the first in row-major order."""
+    sc = W.dna_scoring()
+    A = np.zeros(100, np.uint8)
+    _score_case(ctx, oracle_mod, A, A[:4], sc.matrix, sc.gap_open, sc.gap_extend)   # one column, rows 4..100
+    _score_case(ctx, oracle_mod, A[:4], A, sc.matrix, sc.gap_open, sc.gap_extend)   # one row, columns 4..100
+    g = np.random.default_rng(W.BASE_SEED + 8300)
+    for period in (2, 3, 5):
+        for t in range(6):
+            unit = g.integers(0, 4, size=period).astype(np.uint8)
+            rep = np.tile(unit, 12 + t)
+            a = np.concatenate([W.uniform_dna(int(g.integers(0, 900)), W.BASE_SEED + 8310 + t), rep,
+                                W.uniform_dna(int(g.integers(0, 900)), W.BASE_SEED + 8320 + t)])
+            b = np.concatenate([W.uniform_dna(int(g.integers(0, 300)), W.BASE_SEED + 8330 + t),
+                                rep[: len(rep) - period * (t % 3)],
+                                W.uniform_dna(int(g.integers(0, 300)), W.BASE_SEED + 8340 + t)])
+            _score_case(ctx, oracle_mod, a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+            _score_case(ctx, oracle_mod, b, a, sc.matrix, sc.gap_open, sc.gap_extend)
+
+
+def test_score_above_16_bits(ctx, oracle_mod):
+    """Scores far above 32,767: the packed fill keeps its values relative to a
+    moving base and must still give exact scores and end cells."""
+    sc = W.dna_scoring()
+    a = W.uniform_dna(45_000, W.BASE_SEED + 8400)
+    b = W.mutate(a, 4, W.BASE_SEED + 8401, p_sub=0.01, p_indel=0.001)
+    _score_case(ctx, oracle_mod, a, a, sc.matrix, sc.gap_open, sc.gap_extend)
+    _score_case(ctx, oracle_mod, a, b, sc.matrix, sc.gap_open, sc.gap_extend)
+    p = W.protein_scoring()
+    q = W.random_protein(8_000, W.BASE_SEED + 8402)
+    r = W.mutate(q, 20, W.BASE_SEED + 8403, p_sub=0.05, p_indel=0.005)
+    _score_case(ctx, oracle_mod, q, r, p.matrix, p.gap_open, p.gap_extend)
+    # a high-scoring region that ends, then a long low stretch, then a second one
+    c = np.concatenate([a[:36_000], W.uniform_dna(20_000, W.BASE_SEED + 8404), a[36_000:40_000]])
+    _score_case(ctx, oracle_mod, c, a[:40_000], sc.matrix, sc.gap_open, sc.gap_extend)
 
 
 @pytest.mark.parametrize("seed", range(6))
@@ -220,11 +283,14 @@ def test_align_paths_cross_tiles(ctx, oracle_mod, case):
     assert got.cigar == want.cigar
 
 
-@pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1", "12,4", "4,4"])
+@pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1", "12,4", "4,4",
+                                 "8,4,0,2,1", "12,4,0,2,1", "16,4,0,2,1", "12,4,2,2,1"])
 def test_strip_heights(oracle_mod, monkeypatch, fwd):
-    """Forward strips of 1280, 1536, 768, 512, 1536 (12 rows a lane) and 512 rows: strip bottoms, row
-    checkpoints and traceback tiles (sides that are multiples of both strip
-    heights) must still meet exactly."""
+    """Forward strips of 1280, 1536, 768, 512, 1536 (12 rows a lane) and 512 rows, and the packed
+    16-bit fill with 8, 12 and 16 rows a lane (two-positions checkpoint columns entered by the
+    int32 traceback tiles), one of them with strips of two warps: strip bottoms, row
+    checkpoints and traceback tiles (sides that are multiples of both strip heights) must
+    still meet exactly."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
     monkeypatch.setenv("SWGB_FWD", fwd)
