@@ -92,6 +92,11 @@ class OracleLib:
         lib.oracle_encode.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64, u8p, i64p]
         lib.oracle_nw_score.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, u8p,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
+        lib.oracle_align_alg.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, u8p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, i64p, i64p,
+                                         i64p, i64p, ctypes.c_char_p, i64p]
+        lib.oracle_score_alg.argtypes = [u8p, ctypes.c_int64, u8p, ctypes.c_int64, u8p, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
         self.lib = lib
 
     def sw_score(self, a, b, S, gap_open: int, gap_extend: int):
@@ -114,6 +119,30 @@ class OracleLib:
         if rc != 0:
             raise ValueError("oracle_nw_score failed (%d)" % rc)
         return sc.value
+
+    def align_alg(self, a, b, S, gap_open: int, gap_extend: int, alg: int) -> Alignment:
+        """Canonical alignment of algorithm alg (0 SW, 1 NW, 2 HW, 3 OV) from full matrices."""
+        a, b, S = _u8(a), _u8(b), _mat(S)
+        ops = ctypes.create_string_buffer(a.size + b.size + 1)
+        vals = [ctypes.c_int64() for _ in range(6)]
+        rc = self.lib.oracle_align_alg(_ptr(a), a.size, _ptr(b), b.size, S.ctypes.data, S.shape[0],
+                                       int(gap_open), int(gap_extend), int(alg),
+                                       *[ctypes.byref(v) for v in vals[:5]], ops, ctypes.byref(vals[5]))
+        if rc != 0:
+            raise ValueError("oracle_align_alg failed with %d" % rc)
+        score, ab, ae, bb, be, nops = (v.value for v in vals)
+        return Alignment(score, ab, ae, bb, be, cigar_from_ops(ops.raw[:nops].decode()))
+
+    def score_alg(self, a, b, S, gap_open: int, gap_extend: int, alg: int):
+        """(score, a_end, b_end) of algorithm alg in linear memory."""
+        a, b, S = _u8(a), _u8(b), _mat(S)
+        sc, ae, be = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        rc = self.lib.oracle_score_alg(_ptr(a), a.size, _ptr(b), b.size, S.ctypes.data, S.shape[0],
+                                       int(gap_open), int(gap_extend), int(alg),
+                                       ctypes.byref(sc), ctypes.byref(ae), ctypes.byref(be))
+        if rc != 0:
+            raise ValueError("oracle_score_alg failed with %d" % rc)
+        return sc.value, ae.value, be.value
 
     def _align(self, fn, a, b, S, gap_open, gap_extend) -> Alignment:
         a, b, S = _u8(a), _u8(b), _mat(S)
@@ -180,6 +209,21 @@ def nw_score(a, b, S, gap_open: int, gap_extend: int) -> int:
 def encode(alphabet: str, text: str) -> np.ndarray:
     """Residue codes of ``text`` in ``alphabet``."""
     return _get().encode(alphabet, text)
+
+
+# The algorithms of paper Section 2.1: local (Smith-Waterman), global
+# (Needleman-Wunsch), semi-global (all of a inside b) and overlap.
+ALG_SW, ALG_NW, ALG_HW, ALG_OV = 0, 1, 2, 3
+
+
+def align_alg(a, b, S, gap_open: int, gap_extend: int, alg: int) -> Alignment:
+    """Canonical alignment of one of the four algorithms (full matrices)."""
+    return _get().align_alg(a, b, S, gap_open, gap_extend, alg)
+
+
+def score_alg(a, b, S, gap_open: int, gap_extend: int, alg: int):
+    """(score, a_end, b_end) of one of the four algorithms (linear memory)."""
+    return _get().score_alg(a, b, S, gap_open, gap_extend, alg)
 
 
 def db_scores(query, subjects, S, gap_open: int, gap_extend: int) -> np.ndarray:

@@ -325,6 +325,196 @@ int oracle_sw_align_ptr(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
 }
 
 /*
+ * The four algorithms of the paper's Section 2.1 (SW, NW, HW, OV), written
+ * out as one full-matrix dynamic programme per algorithm.  The paper
+ * describes them in words only; this file takes these readings:
+ *
+ *   SW (alg 0)  local: the Smith-Waterman recurrence above (zero floor,
+ *               best cell anywhere).
+ *   NW (alg 1)  global: every residue of a and of b is aligned.  Borders
+ *               H(0,0) = 0, H(i,0) = -(o + (i-1)e), H(0,j) = -(o + (j-1)e);
+ *               no zero floor; the end cell is (m, n).
+ *   HW (alg 2)  semi-global: all of a is aligned against a substring of b,
+ *               so gaps before and after it in b are free.  Borders
+ *               H(0,j) = 0, H(i,0) = -(o + (i-1)e); no zero floor; the end
+ *               cell is the best of the last row H(m, j), j = 0 .. n.
+ *   OV (alg 3)  overlap: leading and trailing gaps of both sequences are
+ *               free.  Borders H(0,j) = H(i,0) = 0; no zero floor; the end
+ *               cell is the best of the last row and the last column.
+ *
+ * In every algorithm E(i,0) = F(0,j) = -infinity and the interior cells
+ * follow the Gotoh recurrence (E, F as above; H the maximum of diagonal, E
+ * and F, plus 0 for SW only).  Among equal maxima the end cell is the
+ * first in row-major order (smallest row, then smallest column).  The
+ * traceback starts at the end cell in state H with the SW priorities
+ * (diagonal, then E, then F; inside a gap leave it before extending it)
+ * and stops where the algorithm lets an alignment start: SW at a cell with
+ * H = 0 (or the border), NW at (0, 0), HW at row 0, OV at row 0 or column
+ * 0.  At a border cell that is not a free start the rest of the path is
+ * forced: (i, 0) is reached by i deletions from (0, 0) and (0, j) by j
+ * insertions.
+ *
+ * oracle_align_alg stores H, E and F for every cell (24 bytes per cell);
+ * oracle_score_alg keeps two rows and returns the score and end cell only.
+ * alg outside 0..3 is an argument error.
+ */
+static int64_t border_gap(int64_t k, int o, int e) { return k == 0 ? 0 : -((int64_t)o + (k - 1) * (int64_t)e); }
+
+static int64_t left_border(int alg, int64_t i, int o, int e) {   /* H(i, 0) */
+    return (alg == 1 || alg == 2) ? border_gap(i, o, e) : 0;
+}
+
+static int64_t top_border(int alg, int64_t j, int o, int e) {    /* H(0, j) */
+    return alg == 1 ? border_gap(j, o, e) : 0;
+}
+
+/* Is (i, j) a cell where an alignment of algorithm alg may end? */
+static int end_allowed(int alg, int64_t i, int64_t j, int64_t m, int64_t n) {
+    switch (alg) {
+        case 0: return i > 0 && j > 0;
+        case 1: return i == m && j == n;
+        case 2: return i == m;
+        default: return i == m || j == n;
+    }
+}
+
+int oracle_align_alg(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                     const int8_t *S, int K, int o, int e, int alg,
+                     int64_t *score, int64_t *a_begin, int64_t *a_end,
+                     int64_t *b_begin, int64_t *b_end, char *ops, int64_t *n_ops)
+{
+    if (!args_ok(a, m, b, n, S, K, o, e) || alg < 0 || alg > 3 || !score || !a_begin || !a_end ||
+        !b_begin || !b_end || !n_ops || (m + n > 0 && !ops)) return -1;
+    const int64_t W = n + 1;
+    const size_t cells = (size_t)(m + 1) * (size_t)W;
+    int64_t *H = (int64_t *)malloc(sizeof(int64_t) * cells);
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * cells);
+    int64_t *F = (int64_t *)malloc(sizeof(int64_t) * cells);
+    char *rev = (char *)malloc((size_t)(m + n + 1));
+    if (!H || !E || !F || !rev) { free(H); free(E); free(F); free(rev); return -2; }
+#define AT(X, i, j) X[(size_t)(i) * (size_t)W + (size_t)(j)]
+    for (int64_t j = 0; j <= n; j++) { AT(H, 0, j) = top_border(alg, j, o, e); AT(E, 0, j) = ORACLE_NEG_INF; AT(F, 0, j) = ORACLE_NEG_INF; }
+    for (int64_t i = 0; i <= m; i++) { AT(H, i, 0) = left_border(alg, i, o, e); AT(E, i, 0) = ORACLE_NEG_INF; AT(F, i, 0) = ORACLE_NEG_INF; }
+    for (int64_t i = 1; i <= m; i++) {
+        for (int64_t j = 1; j <= n; j++) {
+            AT(E, i, j) = max2(AT(E, i, j - 1) - e, AT(H, i, j - 1) - o);
+            AT(F, i, j) = max2(AT(F, i - 1, j) - e, AT(H, i - 1, j) - o);
+            int64_t h = AT(H, i - 1, j - 1) + S[a[i - 1] * K + b[j - 1]];
+            h = max2(h, AT(E, i, j));
+            h = max2(h, AT(F, i, j));
+            if (alg == 0) h = max2(h, 0);
+            AT(H, i, j) = h;
+        }
+    }
+    /* end cell: the first maximum in row-major order among the allowed cells
+       (SW: only positive scores; score 0 means the empty alignment) */
+    int found = 0;
+    int64_t best = 0, bi = 0, bj = 0;
+    for (int64_t i = 0; i <= m; i++)
+        for (int64_t j = 0; j <= n; j++) {
+            if (!end_allowed(alg, i, j, m, n)) continue;
+            const int64_t h = AT(H, i, j);
+            if (alg == 0 && h <= 0) continue;
+            if (!found || h > best) { best = h; bi = i; bj = j; found = 1; }
+        }
+    int64_t i = bi, j = bj, k = 0;
+    if (found) {
+        int state = 0;      /* 0 = H, 1 = E, 2 = F */
+        for (;;) {
+            if (state == 0) {
+                const int64_t h = AT(H, i, j);
+                if (alg == 0 && h == 0) break;
+                if (i == 0 && j == 0) break;
+                if (i == 0) {                              /* top border */
+                    if (alg != 1) break;                   /* a free start for HW and OV */
+                    while (j > 0) { rev[k++] = 'I'; j--; }
+                    break;
+                }
+                if (j == 0) {                              /* left border */
+                    if (alg == 0 || alg == 3) break;       /* a free start for SW and OV */
+                    while (i > 0) { rev[k++] = 'D'; i--; }
+                    break;
+                }
+                if (h == AT(H, i - 1, j - 1) + S[a[i - 1] * K + b[j - 1]]) {
+                    rev[k++] = 'M'; i--; j--;
+                } else if (h == AT(E, i, j)) {
+                    state = 1;
+                } else {
+                    state = 2;
+                }
+            } else if (state == 1) {
+                rev[k++] = 'I';
+                if (AT(E, i, j) == AT(H, i, j - 1) - o) state = 0;
+                j--;
+            } else {
+                rev[k++] = 'D';
+                if (AT(F, i, j) == AT(H, i - 1, j) - o) state = 0;
+                i--;
+            }
+        }
+    }
+#undef AT
+    for (int64_t t = 0; t < k; t++) ops[t] = rev[k - 1 - t];
+    *n_ops = k;
+    *score = found ? best : 0;
+    *a_end = found ? bi : 0;
+    *b_end = found ? bj : 0;
+    *a_begin = found ? i : 0;
+    *b_begin = found ? j : 0;
+    free(H); free(E); free(F); free(rev);
+    return 0;
+}
+
+int oracle_score_alg(const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
+                     const int8_t *S, int K, int o, int e, int alg,
+                     int64_t *score, int64_t *a_end, int64_t *b_end)
+{
+    if (!args_ok(a, m, b, n, S, K, o, e) || alg < 0 || alg > 3 || !score || !a_end || !b_end) return -1;
+    int64_t *Hrow = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *Frow = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!Hrow || !Frow) { free(Hrow); free(Frow); return -2; }
+    int found = 0;
+    int64_t best = 0, bi = 0, bj = 0;
+    for (int64_t j = 0; j <= n; j++) {
+        Hrow[j] = top_border(alg, j, o, e);
+        Frow[j] = ORACLE_NEG_INF;
+        if (end_allowed(alg, 0, j, m, n) && (alg != 0) && (!found || Hrow[j] > best)) {
+            best = Hrow[j]; bi = 0; bj = j; found = 1;
+        }
+    }
+    for (int64_t i = 1; i <= m; i++) {
+        int64_t Ecur = ORACLE_NEG_INF;
+        int64_t Hleft = left_border(alg, i, o, e);
+        int64_t Hdiag = Hrow[0];
+        Hrow[0] = Hleft;
+        if (alg != 0 && end_allowed(alg, i, 0, m, n) && (!found || Hleft > best)) {
+            best = Hleft; bi = i; bj = 0; found = 1;
+        }
+        for (int64_t j = 1; j <= n; j++) {
+            const int64_t Hup = Hrow[j];
+            Ecur = max2(Ecur - e, Hleft - o);
+            const int64_t Fcur = max2(Frow[j] - e, Hup - o);
+            int64_t h = Hdiag + S[a[i - 1] * K + b[j - 1]];
+            h = max2(h, Ecur);
+            h = max2(h, Fcur);
+            if (alg == 0) h = max2(h, 0);
+            Frow[j] = Fcur;
+            Hdiag = Hup;
+            Hrow[j] = h;
+            Hleft = h;
+            if (end_allowed(alg, i, j, m, n) && !(alg == 0 && h <= 0) && (!found || h > best)) {
+                best = h; bi = i; bj = j; found = 1;
+            }
+        }
+    }
+    free(Hrow); free(Frow);
+    *score = found ? best : 0;
+    *a_end = found ? bi : 0;
+    *b_end = found ? bj : 0;
+    return 0;
+}
+
+/*
  * Residue encoding: codes[k] = position of text[k] in the alphabet string
  * (case-insensitive for letters), or -1 in *bad_index for the first
  * character that is not in it.  Returns 0, or 1 when a character was not

@@ -131,3 +131,55 @@ def rescore(a, b, S, go, ge, a_begin, b_begin, cigar):
             raise ValueError("bad CIGAR op %r" % ch)
     assert num == ""
     return sc, i, j
+
+
+def _starts(alg, m, n):
+    """Cells where an alignment of algorithm alg may start (NW, HW, OV)."""
+    if alg == 1:
+        return [(0, 0)]
+    if alg == 2:
+        return [(0, j) for j in range(n + 1)]
+    return sorted(set([(i, 0) for i in range(m + 1)] + [(0, j) for j in range(n + 1)]))
+
+
+def _end_ok(alg, i, j, m, n):
+    if alg == 1:
+        return i == m and j == n
+    if alg == 2:
+        return i == m
+    return i == m or j == n
+
+
+def brute_force_alg(a, b, S, go, ge, alg):
+    """Best score, canonical end cell and canonical alignment of the global
+    (alg 1), semi-global (alg 2, all of a inside b) or overlap (alg 3)
+    problem, by listing every alignment that starts where the algorithm lets
+    one start and ends where it lets one end, scored from the definition.
+
+    Returns (score, a_end, b_end, (a_begin, b_begin, ops)).  The end cell is
+    the smallest row, then column, among optimal alignments; the canonical
+    alignment is the optimal one ending there whose backward walk is
+    lexicographically smallest by rank (backward_moves).
+    """
+    m, n = len(a), len(b)
+    best = None
+    cands = []
+    for i0, j0 in _starts(alg, m, n):
+        stack = [(i0, j0, "", 0, "")]
+        while stack:
+            i, j, last, sc, ops = stack.pop()
+            if _end_ok(alg, i, j, m, n):
+                if best is None or sc > best:
+                    best, cands = sc, [(i0, j0, i, j, ops)]
+                elif sc == best:
+                    cands.append((i0, j0, i, j, ops))
+            if i < m and j < n:
+                stack.append((i + 1, j + 1, "M", sc + int(S[a[i]][b[j]]), ops + "M"))
+            if j < n:
+                stack.append((i, j + 1, "I", sc - (ge if last == "I" else go), ops + "I"))
+            if i < m:
+                stack.append((i + 1, j, "D", sc - (ge if last == "D" else go), ops + "D"))
+    i_end, j_end = min((c[2], c[3]) for c in cands)
+    at_end = [c for c in cands if c[2] == i_end and c[3] == j_end]
+    canon = min(at_end, key=lambda c: backward_moves(c[4]))
+    return best, i_end, j_end, (canon[0], canon[1], canon[4])

@@ -41,6 +41,18 @@ MUTANTS = [
     ("no stop at zero (full)", "                if (h == 0) break;\n", "                if (i == 0 || j == 0) break;\n"),
     ("leading gap priced per letter (global)", "        Hrow[0] = -(o + (i - 1) * (int64_t)e);",
      "        Hrow[0] = -(i * (int64_t)e);"),
+    ("semi-global top border penalised", "    return alg == 1 ? border_gap(j, o, e) : 0;",
+     "    return (alg == 1 || alg == 2) ? border_gap(j, o, e) : 0;"),
+    ("semi-global left border free", "    return (alg == 1 || alg == 2) ? border_gap(i, o, e) : 0;",
+     "    return alg == 1 ? border_gap(i, o, e) : 0;"),
+    ("overlap ends in the last row only", "        default: return i == m || j == n;",
+     "        default: return i == m;"),
+    ("zero floor in the variant recurrence", "            if (alg == 0) h = max2(h, 0);\n            AT(H, i, j) = h;",
+     "            if (alg <= 1) h = max2(h, 0);\n            AT(H, i, j) = h;"),
+    ("variant end cell: last maximum", "            if (!found || h > best) { best = h; bi = i; bj = j; found = 1; }",
+     "            if (!found || h >= best) { best = h; bi = i; bj = j; found = 1; }"),
+    ("global border run not forced", "                    while (i > 0) { rev[k++] = 'D'; i--; }",
+     "                    i = 0;"),
     ("zero floor in the global score", "            H = max2(H, F);\n            Frow[j] = F;\n            Hdiag = Hup;\n            Hrow[j] = H;\n            Hleft = H;\n        }\n        Hrow[0]",
      "            H = max2(H, F);\n            H = max2(H, 0);\n            Frow[j] = F;\n            Hdiag = Hup;\n            Hrow[j] = H;\n            Hleft = H;\n        }\n        Hrow[0]"),
 ]
@@ -60,6 +72,9 @@ def _battery(lib):
         ("rescoring", lambda: pins.test_rescoring_medium_cases(lib)),
         ("global-bruteforce", lambda: pins.test_global_score_bruteforce(lib)),
         ("global-closed", lambda: pins.test_global_score_closed_forms(lib)),
+        ("variants-bruteforce", lambda: pins.check_variants_bruteforce(lib, cases=60)),
+        ("variants-closed", lambda: pins.check_variants_closed_forms(lib)),
+        ("variants-rescoring", lambda: pins.check_variants_symmetry_and_rescoring(lib)),
     ]
     for name, fn in checks:
         try:
@@ -88,14 +103,49 @@ def _battery_in_child(so_path):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+# Mutants whose text also occurs in another function name that function:
+# the mistake is planted in its body only.
+SCOPED = {
+    "wrong diagonal index (full)": "int oracle_sw_align_full(",
+    "E opens with extend (full traceback)": "int oracle_sw_align_full(",
+    "F before E (full traceback)": "int oracle_sw_align_full(",
+    "wrong diagonal index (variants)": "int oracle_align_alg(",
+    "E opens with extend (variants)": "int oracle_align_alg(",
+    "F before E (variants)": "int oracle_align_alg(",
+}
+MUTANTS += [
+    ("wrong diagonal index (variants)", "int64_t h = AT(H, i - 1, j - 1) + S[a[i - 1] * K + b[j - 1]];",
+     "int64_t h = AT(H, i - 1, j) + S[a[i - 1] * K + b[j - 1]];"),
+    ("E opens with extend (variants)", "if (AT(E, i, j) == AT(H, i, j - 1) - o) state = 0;",
+     "if (AT(E, i, j) == AT(H, i, j - 1) - e) state = 0;"),
+    ("F before E (variants)",
+     "                } else if (h == AT(E, i, j)) {\n                    state = 1;\n"
+     "                } else {\n                    state = 2;",
+     "                } else if (h == AT(F, i, j)) {\n                    state = 2;\n"
+     "                } else {\n                    state = 1;"),
+]
+
+
+def _plant(src, name, orig, bad):
+    """The source with the mistake planted: orig must occur exactly once in
+    the whole file, or, for a scoped mutant, exactly once in its function."""
+    if name not in SCOPED:
+        assert src.count(orig) == 1, name
+        return src.replace(orig, bad)
+    start = src.index(SCOPED[name])
+    end = src.index("\n}\n", start)
+    body = src[start:end]
+    assert body.count(orig) == 1, name
+    return src[:start] + body.replace(orig, bad) + src[end:]
+
+
 @pytest.mark.parametrize("name,orig,bad", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_mutant_is_caught(name, orig, bad):
     src = open(O.SOURCE).read()
-    assert src.count(orig) == 1, name
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "mutant.c")
         with open(c, "w") as f:
-            f.write(src.replace(orig, bad))
+            f.write(_plant(src, name, orig, bad))
         so = O.compile_source(c, os.path.join(d, "mutant.so"))
         failed = _battery_in_child(so)
     assert failed, "planted mistake %r was not caught by any pin" % name

@@ -281,3 +281,105 @@ def check_top_k(top_k):
 
 def test_top_k_hand_written_rankings(oracle_mod):
     check_top_k(oracle_mod.top_k)
+
+
+# ---- the global (NW), semi-global (HW) and overlap (OV) algorithms of Section 2.1
+
+ALGS = (1, 2, 3)
+
+
+def check_variants_bruteforce(oracle_mod, cases=120, seed=W.BASE_SEED + 7300):
+    """Every NW / HW / OV alignment of tiny pairs, listed and scored from the
+    definition: best score, canonical end cell and canonical path."""
+    from bruteforce import brute_force_alg
+    g = np.random.default_rng(seed)
+    for _ in range(cases):
+        K = int(g.choice([2, 4]))
+        m, n = int(g.integers(0, 5)), int(g.integers(0, 5))
+        a = g.integers(0, K, size=m).astype(np.uint8)
+        b = g.integers(0, K, size=n).astype(np.uint8)
+        S = g.integers(-4, 6, size=(K, K)).astype(np.int8)
+        o = int(g.integers(0, 7))
+        e = int(g.integers(0, o + 1))
+        for alg in ALGS:
+            sc, ie, je, canon = brute_force_alg(list(a), list(b), S, o, e, alg)
+            aln = oracle_mod.align_alg(a, b, S, o, e, alg)
+            assert (aln.score, aln.a_end, aln.b_end) == (sc, ie, je), (alg, list(a), list(b), S.tolist(), o, e)
+            assert oracle_mod.score_alg(a, b, S, o, e, alg) == (sc, ie, je)
+            if e < o:
+                ops = oracle_mod.cigar_from_ops(canon[2])
+                assert (aln.a_begin, aln.b_begin, aln.cigar) == (canon[0], canon[1], ops), (alg, list(a), list(b))
+
+
+def test_variants_bruteforce(oracle_mod):
+    check_variants_bruteforce(oracle_mod)
+
+
+def test_variants_local_equals_sw(oracle_mod):
+    """Algorithm 0 through the variant entry points is the Smith-Waterman oracle."""
+    g = np.random.default_rng(W.BASE_SEED + 7310)
+    for _ in range(40):
+        a, b, S, o, e = _rand_case(g, 4, 60)
+        assert oracle_mod.score_alg(a, b, S, o, e, 0) == oracle_mod.sw_score(a, b, S, o, e)
+        assert oracle_mod.align_alg(a, b, S, o, e, 0) == oracle_mod.sw_align(a, b, S, o, e)
+
+
+def check_variants_closed_forms(oracle_mod):
+    S = W.dna_matrix()
+    a = W.uniform_dna(200, W.BASE_SEED + 7320)
+    # global: identity end to end; one side empty costs one gap; equals the global score function
+    def tup(x):
+        return (x.score, x.a_begin, x.a_end, x.b_begin, x.b_end, x.cigar)
+    assert tup(oracle_mod.align_alg(a, a, S, 5, 2, 1)) == (200, 0, 200, 0, 200, "200M")
+    assert tup(oracle_mod.align_alg(a[:7], a[:0], S, 5, 2, 1)) == (-(5 + 6 * 2), 0, 7, 0, 0, "7D")
+    assert tup(oracle_mod.align_alg(a[:0], a[:9], S, 5, 2, 1)) == (-(5 + 8 * 2), 0, 0, 0, 9, "9I")
+    b = W.mutate(a, 4, W.BASE_SEED + 7321, p_sub=0.1, p_indel=0.02)
+    assert oracle_mod.score_alg(a, b, S, 5, 2, 1)[0] == oracle_mod.nw_score(a, b, S, 5, 2)
+    # semi-global: a copy of a inside b aligns end to end at no gap cost
+    left, right = W.uniform_dna(37, W.BASE_SEED + 7322), W.uniform_dna(50, W.BASE_SEED + 7323)
+    host = np.concatenate([left, a, right])
+    aln = oracle_mod.align_alg(a, host, S, 5, 2, 2)
+    assert (aln.score, aln.a_begin, aln.a_end, aln.b_begin, aln.b_end, aln.cigar) == (200, 0, 200, 37, 237, "200M")
+    # semi-global with b empty: all of a deleted
+    assert tup(oracle_mod.align_alg(a[:4], a[:0], S, 5, 2, 2)) == (-(5 + 3 * 2), 0, 4, 0, 0, "4D")
+    # overlap: a suffix of a equal to a prefix of b, the rest random: free end gaps on both
+    x = np.concatenate([W.uniform_dna(80, W.BASE_SEED + 7324), a[:120]])
+    y = np.concatenate([a[:120], W.uniform_dna(90, W.BASE_SEED + 7325)])
+    aln = oracle_mod.align_alg(x, y, S, 5, 2, 3)
+    assert aln.score >= 120 and aln.a_end == len(x) and aln.b_begin == 0
+    # overlap of two empty-ish sequences is the empty alignment at (0, n)
+    assert oracle_mod.score_alg(a[:0], a[:5], S, 5, 2, 3) == (0, 0, 0)
+    assert oracle_mod.score_alg(a[:3], a[:0], S, 5, 2, 3) == (0, 0, 0)
+
+
+def test_variants_closed_forms(oracle_mod):
+    check_variants_closed_forms(oracle_mod)
+
+
+def check_variants_symmetry_and_rescoring(oracle_mod):
+    """NW and OV scores are symmetric under swapping the sequences (with the
+    transposed matrix); every variant CIGAR rescores to its score and spans
+    the cells its algorithm requires."""
+    g = np.random.default_rng(W.BASE_SEED + 7330)
+    for t in range(30):
+        K = 4
+        A = g.integers(0, K, size=int(g.integers(1, 90))).astype(np.uint8)
+        B = W.mutate(A, K, W.BASE_SEED + 7340 + t, p_sub=0.2, p_indel=0.05)[: int(g.integers(1, 120))]
+        S = g.integers(-4, 6, size=(K, K)).astype(np.int8)
+        o = int(g.integers(1, 8))
+        e = int(g.integers(0, o + 1))
+        for alg in (1, 3):
+            assert oracle_mod.score_alg(A, B, S, o, e, alg)[0] == oracle_mod.score_alg(B, A, S.T.copy(), o, e, alg)[0]
+        for alg in ALGS:
+            aln = oracle_mod.align_alg(A, B, S, o, e, alg)
+            assert rescore(A, B, S, o, e, aln.a_begin, aln.b_begin, aln.cigar) == (aln.score, aln.a_end, aln.b_end)
+            if alg == 1:
+                assert (aln.a_begin, aln.b_begin, aln.a_end, aln.b_end) == (0, 0, len(A), len(B))
+            elif alg == 2:
+                assert aln.a_begin == 0 and aln.a_end == len(A)
+            else:
+                assert (aln.a_begin == 0 or aln.b_begin == 0) and (aln.a_end == len(A) or aln.b_end == len(B))
+
+
+def test_variants_symmetry_and_rescoring(oracle_mod):
+    check_variants_symmetry_and_rescoring(oracle_mod)
