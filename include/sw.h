@@ -71,19 +71,54 @@ typedef struct sw_ctx sw_ctx;   /* device, stream, scratch memory, tuning state 
 typedef struct sw_db  sw_db;    /* device-resident, length-sorted protein database */
 
 /*
+ * Algorithms (paper Section 2.1: SW# computes local, global, semi-global
+ * and overlap alignments; Sections 2.1.1-2.1.4 name them NW, SW, HW, OV).
+ * The paper describes them in words; this library takes these readings,
+ * with H(0,0) = 0, E(i,0) = F(0,j) = -infinity and the Gotoh recurrence
+ * above in every interior cell:
+ *   SW_ALG_LOCAL       Smith-Waterman: zero floor, best cell anywhere, the
+ *                      traceback stops at H = 0.
+ *   SW_ALG_GLOBAL      Needleman-Wunsch: H(i,0) = -(o + (i-1)e),
+ *                      H(0,j) = -(o + (j-1)e), no zero floor; end cell
+ *                      (m, n), the path starts at (0, 0).
+ *   SW_ALG_SEMIGLOBAL  all of a against a substring of b: H(0,j) = 0,
+ *                      H(i,0) = -(o + (i-1)e), no floor; end cell the best
+ *                      of the last row (j = 0 .. n), the path starts in row 0.
+ *   SW_ALG_OVERLAP     leading and trailing gaps of both sequences free:
+ *                      H(0,j) = H(i,0) = 0, no floor; end cell the best of
+ *                      the last row and the last column, the path starts in
+ *                      row 0 or column 0.
+ * Among equal maxima the end cell is the first in row-major order.  Scores
+ * of the other algorithms may be zero or negative; every coordinate and
+ * CIGAR follows the same conventions as the local one (a path that reaches
+ * column 0 below row 0 in the global or semi-global algorithm, or row 0
+ * right of column 0 in the global one, continues as one deletion or
+ * insertion run to (0, 0)).
+ */
+#define SW_ALG_LOCAL       0
+#define SW_ALG_GLOBAL      1
+#define SW_ALG_SEMIGLOBAL  2
+#define SW_ALG_OVERLAP     3
+
+/*
  * Scoring scheme (paper Sections 2.2 and 3.2: a substitution matrix plus gap
- * open and gap extension penalties).  matrix is alphabet x alphabet int8,
- * row-major, matrix[x*alphabet + y] = score of residue x of a (rows) against
- * residue y of b (columns); it is copied at call time.  Penalties are given
- * as non-negative numbers that are subtracted; 0 <= gap_extend <= gap_open
- * <= 1,000,000 (with gap_extend > gap_open the Gotoh recurrence would not
- * score maximal gap runs as open + (k-1)*extend).  1 <= alphabet <= 32.
+ * open and gap extension penalties, and the algorithm of Section 2.1).
+ * matrix is alphabet x alphabet int8, row-major, matrix[x*alphabet + y] =
+ * score of residue x of a (rows) against residue y of b (columns); it is
+ * copied at call time.  Penalties are given as non-negative numbers that are
+ * subtracted; 0 <= gap_extend <= gap_open <= 1,000,000 (with gap_extend >
+ * gap_open the Gotoh recurrence would not score maximal gap runs as
+ * open + (k-1)*extend).  1 <= alphabet <= 32.  algorithm is one of SW_ALG_*
+ * (a zero-initialised struct is the local algorithm); the pairwise calls
+ * (sw_score, sw_align) and the batch accept all four, the database search,
+ * the server and sw_score_noalloc the local one only (else SW_EINVAL).
  */
 typedef struct {
     int32_t alphabet;
     const int8_t *matrix;
     int32_t gap_open;
     int32_t gap_extend;
+    int32_t algorithm;
 } sw_scoring;
 
 /* Score and canonical end cell of one pair. */
@@ -135,11 +170,13 @@ const char *sw_strerror(int status);
 int sw_encode(sw_ctx *ctx, const char *alphabet, const char *text, int64_t len, uint8_t *codes);
 
 /*
- * Resolution phase for one pair (paper Section 2.2): best local score and
- * its canonical end cell.  0 <= m, n <= SW_MAX_LEN; every code < alphabet.
- * Scores are bounded by min(m, n) * max S(x, y), which must be below 2^26
- * (67,108,864), else SW_ERANGE (the int32 fill tags row indices into the
- * low bits of its scores to pick the canonical end cell without branches).
+ * Resolution phase for one pair (paper Section 2.2): best score of the
+ * scoring's algorithm and its canonical end cell.  0 <= m, n <= SW_MAX_LEN;
+ * every code < alphabet.  Scores are bounded by min(m, n) * max S(x, y),
+ * which must be below 2^26 (67,108,864), else SW_ERANGE (the int32 fill tags
+ * row indices into the low bits of its scores to pick the canonical end cell
+ * without branches); for the algorithms other than the local one the most
+ * negative value, gap_open + (m + n) * gap_extend, must stay below it too.
  */
 int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
              const sw_scoring *sc, sw_hit *out);

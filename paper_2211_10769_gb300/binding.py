@@ -31,7 +31,12 @@ class SwError(RuntimeError):
 
 class _Scoring(ctypes.Structure):
     _fields_ = [("alphabet", ctypes.c_int32), ("matrix", ctypes.c_void_p),
-                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32),
+                ("algorithm", ctypes.c_int32)]
+
+
+# sw_scoring.algorithm (paper Section 2.1): local, global, semi-global, overlap
+ALG_LOCAL, ALG_GLOBAL, ALG_SEMIGLOBAL, ALG_OVERLAP = 0, 1, 2, 3
 
 
 class _Hit(ctypes.Structure):
@@ -125,10 +130,10 @@ def _seq(x):
     return (arr.ctypes.data if arr.size else None), int(arr.size), arr
 
 
-def _scoring(matrix, gap_open: int, gap_extend: int):
+def _scoring(matrix, gap_open: int, gap_extend: int, algorithm: int = ALG_LOCAL):
     mat = np.ascontiguousarray(np.asarray(matrix, dtype=np.int8))
     assert mat.ndim == 2 and mat.shape[0] == mat.shape[1]
-    return _Scoring(mat.shape[0], mat.ctypes.data, int(gap_open), int(gap_extend)), mat
+    return _Scoring(mat.shape[0], mat.ctypes.data, int(gap_open), int(gap_extend), int(algorithm)), mat
 
 
 @dataclass(frozen=True)
@@ -210,19 +215,19 @@ class Context:
                                    out.ctypes.data if out.size else None), "sw_encode")
         return out
 
-    def score(self, a, b, matrix, gap_open: int, gap_extend: int) -> Hit:
+    def score(self, a, b, matrix, gap_open: int, gap_extend: int, algorithm: int = ALG_LOCAL) -> Hit:
         pa, m, ka = _seq(a)
         pb, n, kb = _seq(b)
-        sc, keep = _scoring(matrix, gap_open, gap_extend)
+        sc, keep = _scoring(matrix, gap_open, gap_extend, algorithm)
         hit = _Hit()
         _check(self._lib.sw_score(self.handle, pa, m, pb, n, ctypes.byref(sc), ctypes.byref(hit)),
                "sw_score")
         return Hit(hit.score, hit.a_end, hit.b_end)
 
-    def align(self, a, b, matrix, gap_open: int, gap_extend: int) -> Alignment:
+    def align(self, a, b, matrix, gap_open: int, gap_extend: int, algorithm: int = ALG_LOCAL) -> Alignment:
         pa, m, ka = _seq(a)
         pb, n, kb = _seq(b)
-        sc, keep = _scoring(matrix, gap_open, gap_extend)
+        sc, keep = _scoring(matrix, gap_open, gap_extend, algorithm)
         aln = _Alignment()
         _check(self._lib.sw_align(self.handle, pa, m, pb, n, ctypes.byref(sc), ctypes.byref(aln)),
                "sw_align")
@@ -254,8 +259,8 @@ def _pack_pairs(pairs):
 def _scoring_array(scorings):
     arr = (_Scoring * len(scorings))()
     keep = []
-    for i, (mat, go, ge) in enumerate(scorings):
-        sc, k = _scoring(mat, go, ge)
+    for i, s in enumerate(scorings):           # (matrix, open, extend[, algorithm])
+        sc, k = _scoring(*s)
         arr[i] = sc
         keep.append(k)
     return arr, keep

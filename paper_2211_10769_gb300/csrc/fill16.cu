@@ -58,6 +58,7 @@ int launch16_mode(sw_ctx *c, int mode, const FillLaunch &L, int K, long long tic
 
 bool swgb::p16_fits(const DevScoring &s, int R) {
     if (R != 8 && R != 12 && R != 16) return false;
+    if (s.alg != kAlgLocal) return false;            // the packed fill keeps the zero floor
     int lo = 127, hi = -128;
     for (int k = 0; k < s.K * s.K; ++k) { lo = std::min(lo, (int)s.mat[k]); hi = std::max(hi, (int)s.mat[k]); }
     return p16_spread(R, s.go, s.ge, hi, lo) < kP16Span;

@@ -87,6 +87,7 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     DevScoring ds;
     int rc = check_scoring(sc, &ds);
     if (rc) return rc;
+    if (ds.alg != kAlgLocal) return SW_EINVAL;          // the local algorithm only
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     const long long nstrips = (m + kHC - 1) / kHC;
     if (n > kMaxCols || nstrips > kMaxStrips) return SW_ERANGE;
@@ -141,7 +142,7 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     const long long grid = std::min<long long>(nstrips, (long long)occ * nsm);
     wavefront_kernel<kR, kW, kModeScore, kProf8><<<(unsigned)grid, (kW + 2) * 32, smem, st>>>(L);
     CU(cudaGetLastError());
-    reduce_candidates_kernel<<<1, 32, 0, st>>>(task, 1, cand, result);
+    reduce_candidates_kernel<<<1, 32, 0, st>>>(task, 1, cand, scoring, result);
     CU(cudaGetLastError());
 
     int4 res[2];

@@ -80,6 +80,7 @@ int swgb::check_scoring(const sw_scoring *sc, DevScoring *out) {
     if (!sc || !sc->matrix) return SW_EINVAL;
     if (sc->alphabet < 1 || sc->alphabet > kMaxAlphabet) return SW_EINVAL;
     if (sc->gap_extend < 0 || sc->gap_open < sc->gap_extend || sc->gap_open > 1000000) return SW_EINVAL;
+    if (sc->algorithm < SW_ALG_LOCAL || sc->algorithm > SW_ALG_OVERLAP) return SW_EINVAL;
     if (out) {
         std::memset(out, 0, sizeof(*out));
         const int K = sc->alphabet;
@@ -87,6 +88,7 @@ int swgb::check_scoring(const sw_scoring *sc, DevScoring *out) {
         out->K = K;
         out->go = sc->gap_open;
         out->ge = sc->gap_extend;
+        out->alg = sc->algorithm;
     }
     return SW_OK;
 }
@@ -255,6 +257,7 @@ FillConfig swgb::pair_fill_config(const sw_ctx *c, int64_t rows) {
 // fewest rows per lane in {8, 12, 16} that give at most one strip per SM;
 // else the int32 fill of pair_fill_config.
 FillConfig swgb::pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevScoring &s) {
+    if (s.alg != kAlgLocal) return variant_fill_config(c, rows);
     if (!c->fwd_auto) {
         FillConfig f = c->fwd;
         f.P16 = f.P16 && p16_fits(s, f.R) && f.W == 4;
@@ -297,6 +300,7 @@ int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, con
                       long long tickets) {
     if (tickets <= 0) return SW_OK;
     if (cfg.P16) return launch_fill16(c, cfg, mode, L, K, tickets);
+    if (cfg.alg != kAlgLocal) return launch_fill_variant(c, cfg, mode, fold, L, K, tickets);
     if (cfg.R == 4 && cfg.W == 4) return launch_fill_rw<4, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 4) return launch_fill_rw<8, 4>(c, mode, fold, L, K, tickets, cfg.B);
     if (cfg.R == 8 && cfg.W == 8) return launch_fill_rw<8, 8>(c, mode, fold, L, K, tickets, cfg.B);
@@ -493,8 +497,14 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(check_scoring(sc, &ds));
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
-    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
-    if (m == 0 || n == 0) { *out = sw_hit{0, 0, 0, 0}; return SW_OK; }
+    if (!score_range_ok(sc, m, n)) return SW_ERANGE;
+    if (m == 0 || n == 0) {
+        // an empty side: the local score is 0; the other algorithms end on the border
+        int cs = kNoScore, ci = 0x7fffffff, cj = 0x7fffffff;
+        if (ds.alg != kAlgLocal) border_end_candidates(ds.alg, m, n, ds.go, ds.ge, &cs, &ci, &cj);
+        *out = ds.alg == kAlgLocal ? sw_hit{0, 0, 0, 0} : sw_hit{cs, 0, (int64_t)ci, (int64_t)cj};
+        return SW_OK;
+    }
     DeviceGuard g(c->device);
     const uint8_t *da, *db;
     RC(stage_seq(c, a, m, c->seq_a, &da));
@@ -523,6 +533,7 @@ int sw_score(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,
                                                        static_cast<const int4 *>(c->cand.p),
+                                                       static_cast<const DevScoring *>(c->scorings.p),
                                                        static_cast<int4 *>(c->result.p));
     CU(cudaGetLastError());
     ++c->launches;

@@ -51,6 +51,39 @@ int empty_alignment(sw_alignment *out) {
     return SW_OK;
 }
 
+// The forced part of a path that reaches the matrix border at (i, j) in
+// state H: the global algorithm continues from (i, 0) with i deletions and
+// from (0, j) with j insertions to (0, 0), the semi-global one from (i, 0)
+// with i deletions; the other border cells are free starts.  Returns the
+// CIGAR text of that run ("" when none) and moves (i, j) to where the path
+// starts.
+std::string border_run(int alg, int64_t *i, int64_t *j) {
+    char buf[32];
+    if (*j == 0 && *i > 0 && (alg == kAlgGlobal || alg == kAlgSemiGlobal)) {
+        std::snprintf(buf, sizeof(buf), "%lldD", (long long)*i);
+        *i = 0;
+        return buf;
+    }
+    if (*i == 0 && *j > 0 && alg == kAlgGlobal) {
+        std::snprintf(buf, sizeof(buf), "%lldI", (long long)*j);
+        *j = 0;
+        return buf;
+    }
+    return "";
+}
+
+// An alignment whose end cell (ie, je) lies on the border: only the forced
+// border run, if any.
+int border_alignment(int alg, int score, int64_t ie, int64_t je, sw_alignment *out) {
+    int64_t i = ie, j = je;
+    const std::string cig = border_run(alg, &i, &j);
+    char *s = static_cast<char *>(std::malloc(cig.size() + 1));
+    if (!s) return SW_ENOMEM;
+    std::memcpy(s, cig.c_str(), cig.size() + 1);
+    *out = sw_alignment{score, 0, i, ie, j, je, s, (int64_t)cig.size()};
+    return SW_OK;
+}
+
 template <typename Word, int R>
 int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT) {
     if ((long long)nI * nJ > kWalkTableMax || BT < kWalkMinBT || BT % R != 0) return SW_EINVAL;
@@ -91,8 +124,13 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(check_scoring(sc, &ds));
     if (m < 0 || n < 0 || (m > 0 && !a) || (n > 0 && !b)) return SW_EINVAL;
     if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
-    if ((double)std::min(m, n) * (double)max_pos_score(sc) >= (double)kMaxScoreBound) return SW_ERANGE;
-    if (m == 0 || n == 0) return empty_alignment(out);
+    if (!score_range_ok(sc, m, n)) return SW_ERANGE;
+    if (m == 0 || n == 0) {
+        if (ds.alg == kAlgLocal) return empty_alignment(out);
+        int cs = kNoScore, ci = 0x7fffffff, cj = 0x7fffffff;
+        border_end_candidates(ds.alg, m, n, ds.go, ds.ge, &cs, &ci, &cj);
+        return border_alignment(ds.alg, cs, ci, cj, out);
+    }
     DeviceGuard g(c->device);
     const uint8_t *da, *db;
     RC(stage_seq(c, a, m, c->seq_a, &da));
@@ -112,8 +150,9 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     const int HC = sw * 32 * fwd.R;
     // the traceback tiles continue the forward fill's staircase checkpoint columns lane by
     // lane, so both fills must give each lane the same rows (R)
-    FillConfig tbc = c->tbc.R == fwd.R ? c->tbc : FillConfig{fwd.R, 4};
+    FillConfig tbc = (c->tbc.R == fwd.R && fwd.alg == kAlgLocal) ? c->tbc : FillConfig{fwd.R, 4};
     tbc.P16 = 0;                                  // traceback bits come from the int32 fill
+    tbc.alg = fwd.alg;
     // the packed forward fill stores its checkpoint columns with two positions per lane and
     // one auxiliary record per half-group of R/2 rows
     const int aux_rows = fwd.P16 ? fwd.R / 2 : fwd.R;
@@ -151,6 +190,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->result.ensure(sizeof(int4)));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), 1,
                                                        static_cast<const int4 *>(c->cand.p),
+                                                       static_cast<const DevScoring *>(c->scorings.p),
                                                        static_cast<int4 *>(c->result.p));
     CU(cudaGetLastError());
     ++c->launches;
@@ -163,8 +203,9 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     std::memcpy(&res, c->stage3.p, sizeof(int4));
     std::memcpy(&e, static_cast<char *>(c->stage3.p) + 16, sizeof(int));
     RC(map_kernel_error(e));
-    if (res.x <= 0) return empty_alignment(out);
+    if (ds.alg == kAlgLocal && res.x <= 0) return empty_alignment(out);
     const int ie = res.y, je = res.z;
+    if (ie == 0 || je == 0) return border_alignment(ds.alg, res.x, ie, je, out);   // other algorithms only
 
     // ---- 2. walk state
     RC(c->walk.ensure(sizeof(WalkState)));
@@ -222,6 +263,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;
                 u.ckpt_every = 0; u.ckpt = nullptr; u.colck = nullptr; u.colck_every = 0;
                 u.row0 = (int32_t)r0;
+                u.col0 = (int32_t)c0;
                 u.tb = static_cast<char *>(c->tb.p) + k * tile_bytes;
                 u.tb_ld = BT;
                 tickets += u.nstrips;
@@ -248,13 +290,15 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     }
     if (w.done != 1) return SW_ECUDA;     // the walk must end at a zero cell or the border
 
-    // ---- 4. CIGAR text from the run records (stored end -> start)
+    // ---- 4. CIGAR text from the run records (stored end -> start), after the forced run of a
+    // path that reached the border (the global and semi-global algorithms)
     std::vector<int2> runs((size_t)w.nruns);
     if (w.nruns > 0) {
         CU(cudaMemcpy(runs.data(), c->runs.p, (size_t)w.nruns * sizeof(int2), cudaMemcpyDeviceToHost));
     }
-    std::string cig;
-    cig.reserve((size_t)w.nruns * 6);
+    int64_t bi = w.i, bj = w.j;
+    std::string cig = border_run(ds.alg, &bi, &bj);
+    cig.reserve(cig.size() + (size_t)w.nruns * 6);
     static const char opc[3] = {'M', 'I', 'D'};
     char buf[24];
     for (long long k = w.nruns - 1; k >= 0; --k) {
@@ -266,7 +310,6 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     char *s = static_cast<char *>(std::malloc(cig.size() + 1));
     if (!s) return SW_ENOMEM;
     std::memcpy(s, cig.c_str(), cig.size() + 1);
-    *out = sw_alignment{res.x, 0, (int64_t)w.i, (int64_t)ie, (int64_t)w.j, (int64_t)je, s,
-                        (int64_t)cig.size()};
+    *out = sw_alignment{res.x, 0, bi, (int64_t)ie, bj, (int64_t)je, s, (int64_t)cig.size()};
     return SW_OK;
 }

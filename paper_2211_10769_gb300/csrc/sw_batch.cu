@@ -222,6 +222,7 @@ int enqueue_run(sw_batch *B) {
         L.tasks = static_cast<const FillTask *>(B->tasks.p);
         L.cand = static_cast<int4 *>(B->cand.p);
         reduce_candidates_kernel<<<(B->ntasks + 7) / 8, 256, 0, st>>>(L.tasks, B->ntasks, L.cand,
+                                                                      static_cast<const DevScoring *>(B->meta.p),
                                                                       static_cast<int4 *>(B->res.p));
         CU(cudaGetLastError());
         ++c->launches;
@@ -244,7 +245,16 @@ int finish_run(sw_batch *B, sw_hit *out) {
     std::memcpy(&e, static_cast<char *>(B->host_hits.p) + out_bytes, sizeof(int));
     RC(map_kernel_error(e));
     const int4 *h = static_cast<const int4 *>(B->host_hits.p);
-    for (int64_t p = 0; p < B->npairs; ++p) out[p] = sw_hit{h[p].x, 0, (int64_t)h[p].y, (int64_t)h[p].z};
+    for (int64_t p = 0; p < B->npairs; ++p) {
+        out[p] = sw_hit{h[p].x, 0, (int64_t)h[p].y, (int64_t)h[p].z};
+        const DevScoring &d = B->scorings[(size_t)B->sidx[(size_t)p]];
+        if ((B->m[(size_t)p] == 0 || B->n[(size_t)p] == 0) && d.alg != kAlgLocal) {
+            // pairs with an empty side have no task: their end cell lies on the border
+            int cs = kNoScore, ci = 0x7fffffff, cj = 0x7fffffff;
+            border_end_candidates(d.alg, B->m[(size_t)p], B->n[(size_t)p], d.go, d.ge, &cs, &ci, &cj);
+            out[p] = sw_hit{cs, 0, (int64_t)ci, (int64_t)cj};
+        }
+    }
     return SW_OK;
 }
 
@@ -288,10 +298,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
         const int64_t m = a_off[p + 1] - a_off[p], n = b_off[p + 1] - b_off[p];
         if (m < 0 || n < 0 || scoring_of_pair[p] < 0 || scoring_of_pair[p] >= nscorings) return SW_EINVAL;
         if (m > SW_MAX_LEN || n > SW_MAX_LEN) return SW_ERANGE;
-        int mx = 0;
-        const DevScoring &d = B->scorings[(size_t)scoring_of_pair[p]];
-        for (int k = 0; k < d.K * d.K; ++k) mx = std::max(mx, (int)d.mat[k]);
-        if ((double)std::min(m, n) * (double)mx >= (double)kMaxScoreBound) return SW_ERANGE;
+        if (!score_range_ok(&scorings[scoring_of_pair[p]], m, n)) return SW_ERANGE;
         B->m[(size_t)p] = m;
         B->n[(size_t)p] = n;
     }
@@ -361,7 +368,13 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
             std::stable_sort(bin.pairs.begin(), bin.pairs.end(), [&](int32_t x, int32_t y) { return cells(x) > cells(y); });
         auto bin_cells = [&](const Bin &bin) { double t = 0; for (int32_t p : bin.pairs) t += cells(p); return t; };
         std::stable_sort(bins.begin(), bins.end(), [&](const Bin &x, const Bin &y) { return bin_cells(x) > bin_cells(y); });
-        for (Bin &bin : bins) bin.cfg = c->bat;
+        for (Bin &bin : bins) {
+            bin.cfg = c->bat;
+            if (B->scorings[(size_t)bin.sidx].alg != kAlgLocal) {   // global, semi-global, overlap
+                bin.cfg = FillConfig{bin.rclass ? 16 : 8, 4};
+                bin.cfg.alg = 1;
+            }
+        }
         B->bins = std::move(bins);
         for (size_t k = 0; k < B->bins.size(); ++k) {
             cudaStream_t bs = nullptr;
@@ -380,6 +393,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
     std::vector<bool> tuned(B->bins.size(), false);
     for (size_t k = 0; k < B->bins.size(); ++k) {
         cls[k] = bin_class(B, B->bins[k]);
+        if (B->bins[k].cfg.alg != kAlgLocal) { tuned[k] = true; continue; }   // fixed shapes
         for (const auto &kv : c->batch_tune)
             if (kv.first == cls[k]) { B->bins[k].cfg = kv.second; tuned[k] = true; }
     }

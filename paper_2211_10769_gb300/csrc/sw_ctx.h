@@ -45,6 +45,7 @@ struct FillConfig {
     int S = 0;
     int B = 0;
     int P16 = 0;   // packed 16-bit fill (wavefront16.cuh) instead of the int32 one
+    int alg = 0;   // not kAlgLocal: the int32 fill without the zero floor (fill_variants.cu)
 };
 
 // Device time per kernel kind (sw_ctx_timing): event pairs recorded around
@@ -99,6 +100,12 @@ FillConfig pair_fill_config(const sw_ctx *c, int64_t rows);
 FillConfig pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevScoring &s);   // picks P16 where exact
 bool p16_fits(const DevScoring &s, int R);
 int launch_fill16(sw_ctx *c, const FillConfig &cfg, int mode, const FillLaunch &L, int K, long long tickets);
+// the global, semi-global and overlap algorithms: 8 or 16 rows a lane, four compute warps
+FillConfig variant_fill_config(const sw_ctx *c, int64_t rows);
+int launch_fill_variant(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
+                        long long tickets);
+// the largest |score| the int32 fill keys without overflow, for a pair of these lengths
+bool score_range_ok(const sw_scoring *sc, int64_t m, int64_t n);
 int tb_word_bytes(int R);
 bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
 int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,

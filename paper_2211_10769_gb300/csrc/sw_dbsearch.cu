@@ -341,6 +341,7 @@ int swgb::db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, c
     RC(c->result.ensure((size_t)nt * sizeof(int4)));
     reduce_candidates_kernel<<<(nt + 7) / 8, 256, 0, c->stream>>>(static_cast<const FillTask *>(c->tasks.p), nt,
                                                                   static_cast<const int4 *>(c->cand.p),
+                                                                  static_cast<const DevScoring *>(c->scorings.p),
                                                                   static_cast<int4 *>(c->result.p));
     CU(cudaGetLastError());
     ++c->launches;
@@ -383,6 +384,7 @@ extern "C" int sw_dbsearch(sw_ctx *c, const sw_db *db, const uint8_t *q, int64_t
     if (db->device != c->device) return SW_EINVAL;
     DevScoring ds;
     RC(check_scoring(sc, &ds));
+    if (ds.alg != kAlgLocal) return SW_EINVAL;          // database search: the local algorithm
     if (m < 0 || (m > 0 && !q)) return SW_EINVAL;
     if (m > SW_MAX_LEN) return SW_ERANGE;
     if (db->max_code >= ds.K) return SW_EINVAL;

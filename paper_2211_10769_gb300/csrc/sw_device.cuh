@@ -25,8 +25,59 @@ struct DevScoring {
     int32_t K;
     int32_t go;     // gap open (positive, subtracted)
     int32_t ge;     // gap extend (positive, subtracted)
-    int32_t pad_;
+    int32_t alg;    // kAlgLocal, kAlgGlobal, kAlgSemiGlobal or kAlgOverlap
 };
+
+// The algorithms of paper Section 2.1.  Local: Smith-Waterman (zero floor,
+// best cell anywhere).  Global (NW): all of a against all of b, gaps at the
+// borders charged, end cell (m, n).  Semi-global (HW): all of a against a
+// substring of b, so row 0 is free and the end cell is the best of the last
+// row.  Overlap (OV): rows 0 and column 0 free, end cell the best of the
+// last row and the last column.  No zero floor except for the local one.
+enum Alg { kAlgLocal = 0, kAlgGlobal = 1, kAlgSemiGlobal = 2, kAlgOverlap = 3 };
+
+// Cost of a gap of k letters, o + (k - 1) e, negated; 0 for k = 0.
+__host__ __device__ __forceinline__ long long neg_gap(long long k, int go, int ge) {
+    return k == 0 ? 0 : -((long long)go + (k - 1) * (long long)ge);
+}
+// H of the matrix's left border, H(i, 0), and of its top border, H(0, j).
+__host__ __device__ __forceinline__ long long left_border_h(int alg, long long i, int go, int ge) {
+    return (alg == kAlgGlobal || alg == kAlgSemiGlobal) ? neg_gap(i, go, ge) : 0;
+}
+__host__ __device__ __forceinline__ long long top_border_h(int alg, long long j, int go, int ge) {
+    return alg == kAlgGlobal ? neg_gap(j, go, ge) : 0;
+}
+constexpr int kNoScore = -0x7fffffff - 1;   // no end-cell candidate (the other algorithms' scores may be <= 0)
+
+// Order of end-cell candidates: larger score, then smaller row i, then
+// smaller column j (the first maximum in row-major order).
+__host__ __device__ __forceinline__ bool cand_better(int s1, int j1, int i1, int s2, int j2, int i2) {
+    if (s1 != s2) return s1 > s2;
+    if (i1 != i2) return i1 < i2;
+    return j1 < j2;
+}
+
+// The end cells of the global, semi-global and overlap algorithms that lie
+// on the matrix border (the fill computes rows and columns from 1 on):
+// folded into the candidate (cs, ci, cj) by the same order.  Global: (m, n)
+// when m or n is 0; semi-global: (m, 0); overlap: (0, n), (m, 0), and
+// (0, 0) when m or n is 0 (row 0 or column 0 is then an end line).
+__host__ __device__ inline void border_end_candidates(int alg, long long m, long long n, int go, int ge, int *cs,
+                                                      int *ci, int *cj) {
+    auto take = [&](long long sc, long long i, long long j) {
+        if (cand_better((int)sc, (int)j, (int)i, *cs, *cj, *ci)) { *cs = (int)sc; *ci = (int)i; *cj = (int)j; }
+    };
+    if (alg == kAlgGlobal) {
+        if (m == 0) take(top_border_h(alg, n, go, ge), 0, n);
+        else if (n == 0) take(left_border_h(alg, m, go, ge), m, 0);
+    } else if (alg == kAlgSemiGlobal) {
+        take(left_border_h(alg, m, go, ge), m, 0);
+    } else if (alg == kAlgOverlap) {
+        take(0, 0, n);
+        take(0, m, 0);
+        if (m == 0 || n == 0) take(0, 0, 0);
+    }
+}
 
 // Sign-extend byte k of w to int32 with one byte permute (prmt with the
 // sign-replicate selector bit).
@@ -60,14 +111,6 @@ __device__ __forceinline__ void st_global_4x2_if(unsigned pred, int2 *p, int a0,
 
 __device__ __forceinline__ int ld_volatile(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
-}
-
-// Order of end-cell candidates: larger score, then smaller row i, then
-// smaller column j (the first maximum in row-major order).
-__device__ __forceinline__ bool cand_better(int s1, int j1, int i1, int s2, int j2, int i2) {
-    if (s1 != s2) return s1 > s2;
-    if (i1 != i2) return i1 < i2;
-    return j1 < j2;
 }
 
 }  // namespace swgb

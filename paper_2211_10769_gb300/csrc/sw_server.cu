@@ -115,6 +115,7 @@ extern "C" int sw_server_create(sw_ctx *c, const sw_db *db, const sw_scoring *sc
     if (!c || !db || !out || k < 0 || k > 64 || max_slots < 1 || max_slots > 256 || chunks < 1) return SW_EINVAL;
     DevScoring ds;
     RC(check_scoring(sc, &ds));
+    if (ds.alg != kAlgLocal) return SW_EINVAL;          // the server searches with the local algorithm
     if (!fold_open(ds) || ds.go > 16000 || ds.ge > 16000) return SW_ERANGE;   // needs the packed kernel
     sw_server *S = new (std::nothrow) sw_server();
     if (!S) return SW_ENOMEM;

@@ -75,6 +75,7 @@ struct FillTask {
     int2 *colck_aux;       // the matching left_aux rows: colck_aux + k * (colck_ld / R) + row / R
     int32_t colck_every;   // 0 = none; else store after every colck_every-th column
     int32_t row0;          // row index (0-based, in the whole pair) of the task's first row
+    int32_t col0;          // column index (0-based, in the whole pair) of the task's first column
     int64_t colck_ld;
     void *tb;              // traceback words, TB mode: [row group][tb_ld]
     int64_t tb_ld;
@@ -204,6 +205,8 @@ struct LaneState {
     int U[R], E[R];
     int ub, fb, udiag0;
     int bk, bj;
+    int rlast;        // the other algorithms: the lane's row holding the task's last row, or -1
+    int track;        // ... and whether that row is an end row at every column (semi-global, overlap)
 };
 
 // The lane's end cell is the first of its cells in row-major order holding
@@ -224,7 +227,9 @@ __device__ __forceinline__ int row_key(int u, int r) { return u * kKeyRows + (R 
 // entered with uup / fup = H - open and F of the row above at this column;
 // st.udiag0 holds H - open of the row above at the previous column.  TB
 // collects the four decision bits of every cell into word.
-template <int R, int PK, bool TB>
+// LOCAL: the Smith-Waterman zero floor; without it (the global, semi-global and
+// overlap algorithms) H has no floor and no cell has the "zero" source.
+template <int R, int PK, bool TB, bool LOCAL = true>
 __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int uup, int fup,
                                               int go, int ge, typename TbWord<R>::T &word)
 {
@@ -238,12 +243,13 @@ __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (
         if constexpr (PK == kProf8) sp += go;
         const int uold = st.U[r];                          // H(i,j-1) - open
         const int e = __viaddmax_s32(st.E[r], -ge, uold);
-        const int x = __viaddmax_s32_relu(udiag, sp, e);   // max(H(i-1,j-1) + S, E, 0)
+        const int x = LOCAL ? __viaddmax_s32_relu(udiag, sp, e)  // max(H(i-1,j-1) + S, E, 0)
+                            : __viaddmax_s32(udiag, sp, e);
         const int xgo = x - go;
         const int u = __viaddmax_s32(f, -go, xgo);         // H(i,j) - open
         if constexpr (TB) {
             const int h = u + go, diag = udiag + sp;
-            const unsigned src = h == 0 ? 0u : (h == diag ? 1u : (h == e ? 2u : 3u));
+            const unsigned src = (LOCAL && h == 0) ? 0u : (h == diag ? 1u : (h == e ? 2u : 3u));
             const unsigned nib = src | (e == uold ? 4u : 0u) | (f == fopen_ref ? 8u : 0u);
             word |= (typename TbWord<R>::T)nib << (4 * r);
             fopen_ref = u;
@@ -261,7 +267,7 @@ __device__ __forceinline__ void column_update(LaneState<R> &st, const uint32_t (
 // CHECK handles columns outside [0, n) (the first 31 and last 31 steps of
 // a sweep) where no padding stands in for them (traceback tiles, tasks with
 // a left boundary); every other step skips those tests.
-template <int R, int MODE, int PK, bool CHECK>
+template <int R, int MODE, int PK, bool CHECK, bool LOCAL = true>
 __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int2 top,
                                           int s, int lane, int n, int go, int ge,
                                           int2 *ring_out, typename TbWord<R>::T *tbw)
@@ -272,10 +278,17 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
     if (lane == 0) { uup = top.x; fup = top.y; }
     if (CHECK && (j < 0 || j >= n)) return;
     typename TbWord<R>::T word = 0;
-    column_update<R, PK, MODE == kModeTb>(st, pw, uup, fup, go, ge, word);
+    column_update<R, PK, MODE == kModeTb, LOCAL>(st, pw, uup, fup, go, ge, word);
     if (lane == 31) ring_out[j & (kQS - 1)] = make_int2(st.ub, st.fb);
     if constexpr (MODE == kModeTb) {
         tbw[j] = word;
+    } else if constexpr (!LOCAL) {
+        // semi-global and overlap: the task's last row is an end row at every column
+        int ck = st.bk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) ck = (st.track && r == st.rlast) ? row_key<R>(st.U[r], r) : ck;
+        st.bj = ck > st.bk ? j : st.bj;
+        st.bk = max(st.bk, ck);
     } else {
         int ck = row_key<R>(st.U[0], 0);
 #pragma unroll
@@ -291,7 +304,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
 // column_update restricted to a range of the lane's rows), entered with the
 // row above's H - open and F at this column; udiag = H - open of the row
 // above at the previous column.  Returns the last row's F in *fout.
-template <int R, int PK>
+template <int R, int PK, bool LOCAL>
 __device__ __forceinline__ void rows_update(LaneState<R> &st, const uint32_t (&pw)[ProfWords<R, PK>::N], int r0,
                                             int r1, int uup, int fup, int udiag, int go, int ge, int *fout)
 {
@@ -303,7 +316,7 @@ __device__ __forceinline__ void rows_update(LaneState<R> &st, const uint32_t (&p
         if constexpr (PK == kProf8) sp += go;
         const int uold = st.U[r];
         const int e = __viaddmax_s32(st.E[r], -ge, uold);
-        const int x = __viaddmax_s32_relu(udiag, sp, e);
+        const int x = LOCAL ? __viaddmax_s32_relu(udiag, sp, e) : __viaddmax_s32(udiag, sp, e);
         const int xgo = x - go;
         st.U[r] = __viaddmax_s32(f, -go, xgo);
         st.E[r] = e;
@@ -323,7 +336,7 @@ __device__ __forceinline__ void rows_update(LaneState<R> &st, const uint32_t (&p
 // column c: a 63-step wavefront inside the warp.  Leaves st as the straight
 // boundary column the sweep starts from (U, E per row; ub / fb the last
 // row's H - open and F at c; udiag0 the row above at c for lane 0).
-template <int R, int W, int PK>
+template <int R, int W, int PK, bool LOCAL>
 __device__ __forceinline__ void split_staircase_prologue(const FillTask &T, LaneState<R> &st, const int8_t *prow,
                                                          int grow, int lane, int K, int go, int ge)
 {
@@ -349,14 +362,14 @@ __device__ __forceinline__ void split_staircase_prologue(const FillTask &T, Lane
             uint32_t pwk[NPW];
             load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
             const int uup = st.U[H - 1];
-            rows_update<R, PK>(st, pwk, H, R, uup, fT, udB, go, ge, &fB);
+            rows_update<R, PK, LOCAL>(st, pwk, H, R, uup, fT, udB, go, ge, &fB);
             udB = uup;
         }
         if (k <= 2 * lane) {
             const int cb = min((int)T.b[k - 2 * lane - 1], K);   // column c - 2l + k
             uint32_t pwk[NPW];
             load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
-            rows_update<R, PK>(st, pwk, 0, H, uupT, fupT, udT, go, ge, &fT);
+            rows_update<R, PK, LOCAL>(st, pwk, 0, H, uupT, fupT, udT, go, ge, &fT);
             udT = uupT;
         }
     }
@@ -378,7 +391,7 @@ template <int QS, int QB, int IOB, int SHIFT = 0>
 __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
                                                 int n, int go, int K, int Wa, int lag, int2 *ring0,
                                                 uint8_t *bring, int *prod, const int *cons,
-                                                volatile int *s_abort, int lane)
+                                                volatile int *s_abort, int lane, int alg = kAlgLocal, int ge = 0)
 {
     int in_next = 0;
     long long idle = 0;
@@ -394,7 +407,9 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
         target = min(target, avail_prev);
         if (target > in_next) {
             for (int col = in_next + lane; col < target; col += 32) {
-                const int2 v = src ? __ldcg(src + col) : make_int2(0, kNeg);
+                // the matrix's top border: H(0, j) of the algorithm, F = -infinity
+                const int2 v = src ? __ldcg(src + col)
+                                   : make_int2((int)top_border_h(alg, (long long)T.col0 + col + 1, go, ge), kNeg);
                 if constexpr (SHIFT == 0)
                     ring0[col & (QS - 1)] = make_int2(v.x - go, v.y);
                 else     // scaled values; -infinity stays far below every real value, without overflow
@@ -480,7 +495,8 @@ __device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLa
     }
 }
 
-template <int R, int W, int MODE, int PK>
+// LOCAL = false: the global, semi-global and overlap algorithms (DevScoring::alg)
+template <int R, int W, int MODE, int PK, bool LOCAL = true>
 __global__ void __launch_bounds__((W + 2) * 32) __maxnreg__(R >= 12 ? 128 : (W > 4 ? 96 : 104))
 wavefront_kernel(const FillLaunch L)
 {
@@ -560,13 +576,13 @@ wavefront_kernel(const FillLaunch L)
         if (warp == W) {
             // ================= input warp: top boundary row and residues =================
             fill_input_warp<QS, QB, IOB>(T, L, strip, tk, n, go, K, Wa, 64, ring[0], bring, prod, cons,
-                                         &s_abort, lane);
+                                         &s_abort, lane, LOCAL ? kAlgLocal : SC.alg, ge);
         } else if (warp == W + 1) {
             // ================= output warp: bottom row to global memory =================
             fill_output_warp<QS>(T, L, strip, tk, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
         } else if (warp >= Wa) {
             if constexpr (MODE != kModeTb)
-                if (lane == 0) s_cand[warp] = make_int4(0, 0x7fffffff, 0x7fffffff, 0);
+                if (lane == 0) s_cand[warp] = make_int4(LOCAL ? 0 : kNoScore, 0x7fffffff, 0x7fffffff, 0);
         } else {
             // ================= compute warp =================
             const int lrow = (warp * 32 + lane) * R;        // first row of this lane within the strip
@@ -577,10 +593,18 @@ wavefront_kernel(const FillLaunch L)
 #pragma unroll
             for (int r = 0; r < R; ++r) { st.U[r] = -go; st.E[r] = kNeg; }
             st.udiag0 = -go;                                // matrix border: H = 0
+            if constexpr (!LOCAL) {                         // the algorithm's left border H(i, 0)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    st.U[r] = (int)left_border_h(SC.alg, (long long)T.row0 + grow + r + 1, go, ge) - go;
+                st.udiag0 = (int)left_border_h(SC.alg, (long long)T.row0 + grow, go, ge) - go;
+                st.rlast = (T.rows - 1 >= grow && T.rows - 1 < grow + R) ? T.rows - 1 - grow : -1;
+                st.track = SC.alg == kAlgSemiGlobal || SC.alg == kAlgOverlap;
+            }
             st.ub = st.U[R - 1];
             st.fb = kNeg;
             if (T.left && T.left_split) {
-                split_staircase_prologue<R, W, PK>(T, st, prow, grow, lane, K, go, ge);
+                split_staircase_prologue<R, W, PK, LOCAL>(T, st, prow, grow, lane, K, go, ge);
             } else if (T.left) {
                 // Staircase left boundary: lane l's rows hold column c - l (c = the column
                 // left of the task).  Lane l advances l columns, in step with its neighbours
@@ -601,14 +625,15 @@ wavefront_kernel(const FillLaunch L)
                         uint32_t pwk[NPW];
                         load_profile<R, PK, W * 32>(prow + cb * HC * PB, pwk);
                         typename TbWord<R>::T unused = 0;
-                        column_update<R, PK, false>(st, pwk, uup, fup, go, ge, unused);
+                        column_update<R, PK, false, LOCAL>(st, pwk, uup, fup, go, ge, unused);
                     }
                 }
                 // the diagonal of the task's first column: the row above at column c
                 const int up = __shfl_up_sync(kFull, st.ub, 1);
                 if (lane > 0) st.udiag0 = up;
             }
-            st.bk = row_key<R>(-go, 0); st.bj = -1;      // score 0 never becomes the best
+            // local: score 0 never becomes the best; the other algorithms: any cell of an end row
+            st.bk = LOCAL ? row_key<R>(-go, 0) : kNoScore; st.bj = -1;
             // checkpoint columns (kModeScoreCk): every lane stores at the end of the chunk whose
             // last step is column next_ck for lane 0, so lane l stores column next_ck - l
             int next_ck = (MODE == kModeScoreCk && T.colck && T.colck_every > 0) ? T.colck_every - 1 : 0x7fffffff;
@@ -622,7 +647,7 @@ wavefront_kernel(const FillLaunch L)
             bool loaded = false;             // inputs of step s0 were prefetched by the previous step
             // columns left of the task may be computed (first chunk) only from a border state,
             // and never in traceback mode (their decision words would land outside the tile)
-            const bool virt_ok = MODE != kModeTb && T.left == nullptr;
+            const bool virt_ok = LOCAL && MODE != kModeTb && T.left == nullptr;
             int c;
             uint32_t pw[NPW];
             int2 top;
@@ -658,7 +683,7 @@ wavefront_kernel(const FillLaunch L)
                         const int2 topn = rin[(s + 1) & (QS - 1)];
                         uint32_t pwn[NPW];
                         load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
-                        lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                        lane_step<R, MODE, PK, false, LOCAL>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
                         for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
@@ -683,7 +708,7 @@ wavefront_kernel(const FillLaunch L)
                             const int2 topn = s + 1 < n ? rin[(s + 1) & (QS - 1)] : make_int2(kNeg, kNeg);
                             uint32_t pwn[NPW];
                             load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
-                            lane_step<R, MODE, PK, false>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                            lane_step<R, MODE, PK, false, LOCAL>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
                             for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                             top = topn;
@@ -701,7 +726,7 @@ wavefront_kernel(const FillLaunch L)
                         const int2 topn = rin[(s + 1) & (QS - 1)];   // stale when s + 1 >= n: lane 0 skips that column
                         uint32_t pwn[NPW];
                         load_profile<R, PK, W * 32>(prow + cn * HC * PB, pwn);
-                        lane_step<R, MODE, PK, true>(st, pw, top, s, lane, n, go, ge, rout, tbw);
+                        lane_step<R, MODE, PK, true, LOCAL>(st, pw, top, s, lane, n, go, ge, rout, tbw);
 #pragma unroll
                         for (int q = 0; q < NPW; ++q) pw[q] = pwn[q];
                         top = topn;
@@ -726,10 +751,28 @@ wavefront_kernel(const FillLaunch L)
             }
 
             if constexpr (MODE != kModeTb) {
-                const int br = R - 1 - (st.bk & (kKeyRows - 1));
-                int cs = (st.bk >> 4) + go, cj = st.bj + 1, ci = T.row0 + grow + br + 1;
                 static_assert(kKeyRows == 16, "key decode assumes 4 row bits");
-                if (cs <= 0 || grow + br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
+                int cs, cj, ci;
+                if constexpr (LOCAL) {
+                    const int br = R - 1 - (st.bk & (kKeyRows - 1));
+                    cs = (st.bk >> 4) + go; cj = st.bj + 1; ci = T.row0 + grow + br + 1;
+                    if (cs <= 0 || grow + br >= T.rows) { cs = 0; cj = 0x7fffffff; ci = 0x7fffffff; }
+                } else {
+                    // the best of the task's last row (semi-global, overlap), then the last
+                    // column: every row for the overlap algorithm, the last row for the global one
+                    cs = kNoScore; cj = 0x7fffffff; ci = 0x7fffffff;
+                    if (st.track && st.rlast >= 0 && st.bj >= 0) {
+                        cs = (st.bk >> 4) + go; cj = st.bj + 1; ci = T.row0 + grow + st.rlast + 1;
+                    }
+                    if (n > 0 && (SC.alg == kAlgOverlap || SC.alg == kAlgGlobal)) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const bool end = SC.alg == kAlgOverlap ? grow + r < T.rows : r == st.rlast;
+                            const int sc = st.U[r] + go, ii = T.row0 + grow + r + 1;
+                            if (end && cand_better(sc, n, ii, cs, cj, ci)) { cs = sc; cj = n; ci = ii; }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const int os = __shfl_xor_sync(kFull, cs, off);
@@ -748,7 +791,7 @@ wavefront_kernel(const FillLaunch L)
                     const int4 o = s_cand[w];
                     if (cand_better(o.x, o.z, o.y, b.x, b.z, b.y)) b = o;
                 }
-                b.w = b.x > 0 ? 1 : 0;
+                b.w = LOCAL ? (b.x > 0 ? 1 : 0) : (b.x != kNoScore ? 1 : 0);
                 L.cand[tk] = b;
             }
         }
@@ -758,15 +801,19 @@ wavefront_kernel(const FillLaunch L)
 
 // Reduce the per-strip candidates of every task to one end cell:
 // out[k] = (score, a_end, b_end, 0) with a_end/b_end the 1-based cell
-// (= exclusive 0-based ends), all zero when the best score is 0.
+// (= exclusive 0-based ends); local: all zero when the best score is 0;
+// the other algorithms: the end cells on the matrix border are candidates
+// too (a task is a whole pair there).
 static __global__ void reduce_candidates_kernel(const FillTask *tasks, int ntasks, const int4 *cand,
-                                                int4 *out)
+                                                const DevScoring *scorings, int4 *out)
 {
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= ntasks) return;
     const FillTask &T = tasks[k];
-    int cs = 0, cj = 0x7fffffff, ci = 0x7fffffff;
+    const DevScoring &SC = scorings[T.scoring];
+    const bool local = SC.alg == kAlgLocal;
+    int cs = local ? 0 : kNoScore, cj = 0x7fffffff, ci = 0x7fffffff;
     for (int s = lane; s < T.nstrips; s += 32) {
         const int4 c = cand[T.ticket0 + s];
         if (c.w && cand_better(c.x, c.z, c.y, cs, cj, ci)) { cs = c.x; cj = c.z; ci = c.y; }
@@ -778,7 +825,13 @@ static __global__ void reduce_candidates_kernel(const FillTask *tasks, int ntask
         const int oi = __shfl_xor_sync(kFull, ci, off);
         if (cand_better(os, oj, oi, cs, cj, ci)) { cs = os; cj = oj; ci = oi; }
     }
-    if (lane == 0) out[k] = cs > 0 ? make_int4(cs, ci, cj, 0) : make_int4(0, 0, 0, 0);
+    if (lane != 0) return;
+    if (local) {
+        out[k] = cs > 0 ? make_int4(cs, ci, cj, 0) : make_int4(0, 0, 0, 0);
+    } else {
+        border_end_candidates(SC.alg, T.rows, T.ncols, SC.go, SC.ge, &cs, &ci, &cj);
+        out[k] = make_int4(cs, ci, cj, 0);
+    }
 }
 
 }  // namespace swgb
