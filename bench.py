@@ -36,16 +36,13 @@ import numpy as np  # noqa: E402
 
 from paper_2211_10769_gb300 import workloads as W  # noqa: E402
 
-SM_COUNT_GB300 = 152
 INT_LANES_PER_SM = 128          # 4 sub-partitions x 32 integer lanes
-SM_MAX_MHZ = 2070.0
 OPS_PER_CELL = 10               # E: 2 sub + max, F: 2 sub + max, H: add + 3 max (incl. 0), running max
 WORKLOAD = "dna_pair_200kbp_align"
 # DRAM traffic of the forward fill measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, one full-size launch: 4.36 MB + 378.48 MB over
-# 200,000 x 200,000 cells) per cell, and the kernel source it was taken on.
-FILL_TRAFFIC = {"mode": "align", "bytes_per_cell": (4.36e6 + 378.48e6) / 4.0e10,
-                "source_sha256": "cadc6e19781c7db5963c3eae7c9338aae3655940d8587b8a5a1ade4af4b1f059"}
+# dram__bytes_write.sum of one full-size launch) per cell, and the kernel
+# sources it was taken on (None: not measured on the current kernel).
+FILL_TRAFFIC = None
 
 
 def parse():
@@ -63,9 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--workloads", default="all",
                     help="comma list of the other workloads to measure after the headline: "
-                         "dna2k,dbsearch,batch,serve,dna5m (default all; 'none' for the headline only)")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate (500 = full)")
-    ap.add_argument("--serve-rates", default="50,100,200,500,1000,2000")
+                         "dna2k,variants,dbsearch,batch,serve,dna5m (default all; 'none' for the headline only)")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests per arrival rate")
+    ap.add_argument("--serve-rates", default="10,20,50,2000",
+                    help="arrival rates (requests/s): below, near and above the device's capacity")
     return ap.parse_args()
 
 
@@ -233,7 +231,9 @@ def run_swgb(args, rank, world):
         e2e.append(time.perf_counter() - t0)
     d2h = 48 + len(aln.cigar)
 
-    peak_ops = SM_COUNT_GB300 * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clk.get("sm_max_mhz") or device_max_sm_mhz()
+    peak_ops = nsm * INT_LANES_PER_SM * max_mhz * 1e6
     score_t = statistics.mean(fill_times)
     # the dominant kernel: the forward fill (one launch per step), timed by
     # events recorded around its launches inside the timed steps
@@ -267,7 +267,7 @@ def run_swgb(args, rank, world):
         "e2e": {"value": round(cells / statistics.median(e2e) / 1e9, 2), "unit": "GCUPS",
                 "h2d_bytes_per_step": m + n, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu",
-                     "kernel": "wavefront_kernel, forward fill (%s mode)" % (
+                     "kernel": "wavefront16_kernel (packed 16-bit pair fill), forward fill (%s mode)" % (
                          "checkpoint" if args.mode == "align" else "score"),
                      "achieved": round(achieved / 1e12, 3), "peak": round(peak_ops / 1e12, 3),
                      "unit": "Tint-op/s", "frac": round(achieved / peak_ops, 4),
@@ -275,7 +275,8 @@ def run_swgb(args, rank, world):
                      "ops_per_cell": OPS_PER_CELL, "fill_ms": round(1e3 * fill_t, 3),
                      "fill_launches": fill_n, "fill_gcups": round(cells / fill_t / 1e9, 2),
                      "score_call_gcups": round(cells / score_t / 1e9, 2),
-                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (plain integer ALU issue)"},
+                     "peak_basis": "%d SMs x 128 int32 lanes x %.0f MHz (SM count from the device, "
+                                   "maximum SM clock from nvidia-smi; plain integer ALU issue)" % (nsm, max_mhz)},
         "kernel_ms_per_step": {k: round(v[0] / max(1, args.steps), 3) for k, v in kt.items()},
         "clocks": clk,
     }
@@ -284,15 +285,25 @@ def run_swgb(args, rank, world):
     return out
 
 
+def device_max_sm_mhz():
+    """Maximum SM clock of GPU 0 as nvidia-smi reports it (2070 MHz on GB300 if it cannot be read)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return 2070.0
+
+
 def fill_traffic(m, n, mode):
-    """DRAM bytes (read + write) of one forward-fill launch, from the ncu
-    capture summarised in profiles/wavefront_fill_dna_pair.md, scaled by
-    cells; None once the kernel source differs from the profiled one."""
+    """DRAM bytes (read + write) of one forward-fill launch: an ncu capture
+    of dram__bytes_read.sum + dram__bytes_write.sum on the full-size launch,
+    scaled by cells; None when none was taken on the current kernel sources."""
     if FILL_TRAFFIC is None or mode != FILL_TRAFFIC["mode"]:
         return None
     import hashlib
     h = hashlib.sha256()
-    for f in ("wavefront.cuh", "sw_device.cuh"):
+    for f in ("wavefront16.cuh", "wavefront.cuh", "sw_device.cuh"):
         with open(os.path.join(ROOT, "paper_2211_10769_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest() != FILL_TRAFFIC["source_sha256"]:
@@ -326,7 +337,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "m": len(A), "n": len(B)},
         "cpu_baseline": {"value": round(gcups, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "host_cores": os.cpu_count(), "sample": sample},
         "e2e": {"value": round(gcups, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -341,8 +352,51 @@ def cpu_baseline_leg(args):
     oracle.sw_score(A[:rows], B, sc.matrix, sc.gap_open, sc.gap_extend)
     dt = time.perf_counter() - t0
     return {"value": round(rows * len(B) / dt / 1e9, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle",
-            "sample": "score-only oracle on rows 0..%d of A against all of B (%.2e cells, %.1f s)"
-                      % (rows, rows * len(B), dt)}
+            "host_cores": os.cpu_count(),
+            "sample": "score-only oracle on rows 0..%d of A against all of B (%.2e cells, %.1f s); one pair "
+                      "is one dynamic programme, so one core" % (rows, rows * len(B), dt)}
+
+
+def _threaded_oracle(jobs, fn):
+    """Run fn over jobs on every host core (the oracle is a ctypes call, which
+    releases the interpreter lock, so threads run it in parallel); returns
+    (seconds, threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(fn, jobs))
+    return time.perf_counter() - t0, threads
+
+
+def cpu_workload_legs(wl):
+    """The oracle timed on seeded samples of the database search and of the
+    batch, over all host cores (threads over subjects / pairs), in GCUPS."""
+    from oracle import oracle
+    from paper_2211_10769_gb300 import bench_workloads as BW
+    out = {}
+    g = np.random.default_rng(W.BASE_SEED + 99)
+    if "dbsearch" in wl:
+        sc = W.protein_scoring()
+        qs, pdb = BW._protein_db()
+        q = qs[2]                                        # the 1,000-residue query
+        subj = sorted(g.choice(pdb.nseq, size=20_000, replace=False).tolist())
+        cells = len(q) * sum(len(pdb.subject(s)) for s in subj)
+        dt, th = _threaded_oracle(subj, lambda s: oracle.sw_score(q, pdb.subject(s), sc.matrix, sc.gap_open,
+                                                                   sc.gap_extend))
+        out["dbsearch"] = {"value": round(cells / dt / 1e9, 3), "unit": "GCUPS", "cores": th, "kind": "oracle",
+                           "sample": "query of %d residues against 20,000 seeded subjects of the database "
+                                     "(%.2e cells, %.1f s)" % (len(q), cells, dt)}
+    if "batch" in wl:
+        d, p = W.dna_scoring(), W.protein_scoring()
+        scs = [(d.matrix, d.gap_open, d.gap_extend), (p.matrix, p.gap_open, p.gap_extend)]
+        ks = sorted(g.choice(10_000, size=300, replace=False).tolist())
+        pairs = [W.batch_pair(k) for k in ks]
+        cells = sum(len(a) * len(b) for a, b, _ in pairs)
+        dt, th = _threaded_oracle(pairs, lambda x: oracle.sw_score(x[0], x[1], *scs[0 if x[2] == "dna" else 1]))
+        out["batch"] = {"value": round(cells / dt / 1e9, 3), "unit": "GCUPS", "cores": th, "kind": "oracle",
+                        "sample": "300 seeded pairs of the 10,000 (%.2e cells, %.1f s)" % (cells, dt)}
+    return out
 
 
 def main():
@@ -357,10 +411,14 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(args)
         wl = [] if args.workloads == "none" else (
-            ["dna2k", "dbsearch", "batch", "serve", "dna5m"] if args.workloads == "all" else args.workloads.split(","))
+            ["dna2k", "variants", "dbsearch", "batch", "serve", "dna5m"] if args.workloads == "all"
+            else args.workloads.split(","))
         if wl and args.mode == "align":
             from paper_2211_10769_gb300 import bench_workloads as BW
             out["workloads"] = BW.run_all(wl, args)
+            if not args.no_cpu_baseline:
+                for nm, leg in cpu_workload_legs(wl).items():
+                    out["workloads"][nm]["cpu_baseline"] = leg
         print(json.dumps(out), flush=True)
 
 

@@ -208,9 +208,10 @@ void sw_alignment_free(sw_alignment *aln);
  * fixed array of about 4.3 MB inside the library, which every GPU that
  * loads the library holds until the process exits.  Limits: n <= 262,144
  * columns and m <= 16,384 * 1,024 = 16,777,216 rows; larger inputs are
- * rejected with SW_ERANGE.  The first call on each device looks up the
- * array's device address and must be made with that device current, before
- * any stream capture.  Calls share the array: calls whose GPU work could
+ * rejected with SW_ERANGE.  Every call looks up the array's device address
+ * in the current context (so a device reset between calls is safe); the
+ * first call in a context loads the library's device code and should come
+ * before any stream capture.  Calls share the array: calls whose GPU work could
  * overlap (other streams, other host threads) race and must be serialised
  * by the caller.  Synchronous: returns after the result is on the host.
  */
@@ -234,7 +235,9 @@ int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, const uint8
  *   SW_BATCH_GRAPH     capture each run in a CUDA graph once and replay it;
  *   SW_BATCH_AUTOTUNE  time the candidate tile shapes of every bin on this plan
  *                      and keep the fastest (cached in the context per bin
- *                      size class).
+ *                      size class).  The candidates are int32 lanes of 4-16
+ *                      rows and, for local bins whose scoring keeps it exact,
+ *                      packed 16-bit lanes of 8, 12 or 16 rows.
  * sw_batch_run writes npairs hits (host memory).  A plan belongs to its
  * context and must be destroyed before it.
  */
@@ -249,6 +252,12 @@ void sw_batch_destroy(sw_batch *plan);
 /* Tile shape of the plan's largest bin (by cells): rows per lane and compute
  * warps per block. */
 int sw_batch_config(const sw_batch *plan, int32_t *rows_per_lane, int32_t *warps);
+/* Configuration of bin `bin` of the plan (bins: scoring scheme x row class,
+ * the bin with the most cells first): rows per lane, compute warps per block,
+ * lane width in bits (32, or 16 for the packed fill) and its pair count.
+ * SW_ERANGE once bin is past the last bin; SW_EINVAL on a null pointer. */
+int sw_batch_bin_config(const sw_batch *plan, int32_t bin, int32_t *rows_per_lane, int32_t *warps,
+                        int32_t *lane_bits, int64_t *npairs);
 /* One-shot: create (no graph, no autotuning), run, destroy. */
 int sw_score_batch(sw_ctx *ctx, int64_t npairs, const uint8_t *a_res, const int64_t *a_off,
                    const uint8_t *b_res, const int64_t *b_off, const int32_t *scoring_of_pair,
@@ -297,7 +306,12 @@ int sw_dbsearch(sw_ctx *ctx, const sw_db *db, const uint8_t *q, int64_t m, const
  * (sw_server_poll: SW_EAGAIN while pending; a collected ticket is
  * forgotten).  The scoring must allow the packed 16-bit search (every
  * S + gap_open within int8, penalties <= 16000), else SW_ERANGE at
- * creation; queries longer than 8000 give SW_ERANGE.  k <= 64.  The server
+ * creation; queries longer than 8000 give SW_ERANGE.  k <= 64.  A step runs
+ * its requests in groups of one tile shape each (every query padded to the
+ * passes that fit it best).  A slot keeps its device buffers for the next
+ * request, so the server holds at most max_slots of them; mem_used counts
+ * the active requests' share.  A request whose retirement fails is
+ * retired with that status (sw_server_poll returns it).  The server
  * uses its context's stream and must be destroyed before the context and
  * the database.
  */

@@ -23,6 +23,9 @@ extern "C" {
 #define SW_PROBE_VIMAX3_S16X2_RELU  5   /* __vimax3_s16x2_relu, two 16-bit lanes */
 #define SW_PROBE_PRMT               6   /* byte permute */
 #define SW_PROBE_SHFL               7   /* warp shuffle (plus one xor) */
+#define SW_PROBE_VADDUS4            8   /* __vaddus4: four saturating unsigned 8-bit adds */
+#define SW_PROBE_VSUBUS4            9   /* __vsubus4: four saturating unsigned 8-bit subtracts */
+#define SW_PROBE_VMAXU4            10   /* __vmaxu4: four unsigned 8-bit maxima */
 
 /*
  * Run `op` on every SM (8 blocks of 256 threads per SM, eight independent

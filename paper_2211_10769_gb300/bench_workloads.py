@@ -7,6 +7,8 @@ CUDA events on the context's stream and returns a small dict:
 * dbsearch -- sw_dbsearch of the five protein queries (144 .. 5,478) against
               the 500,000-subject database (top-20), plus its kernel's
               share of the integer peak;
+* variants -- sw_align of the 2 kbp and 200 kbp DNA pairs with each of the
+              four algorithms (local, global, semi-global, overlap);
 * batch    -- sw_batch (one graph-captured, autotuned launch) over the 10,000
               uneven pairs versus one sw_score call per pair;
 * serve    -- the continuous-batching server under Poisson arrivals at each
@@ -23,9 +25,8 @@ import numpy as np
 
 from . import workloads as W
 
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
 OPS_PER_CELL = 10
+REPEATS = 20                  # timed runs per measurement: median and mean are reported
 
 
 _DB_CACHE = {}
@@ -37,6 +38,23 @@ def _protein_db():
         qs = W.protein_queries()
         _DB_CACHE["db"] = (qs, W.protein_db(500_000, queries=qs))
     return _DB_CACHE["db"]
+
+
+def _stats(ts):
+    """Median and mean of a list of seconds."""
+    return statistics.median(ts), statistics.mean(ts)
+
+
+def _int_peak(torch):
+    """Integer-lane issue peak (lanes / s): SMs x 128 x the maximum SM clock."""
+    import subprocess
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        mhz = float(subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                   capture_output=True, text=True, timeout=20).stdout.split()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        mhz = 2070.0
+    return nsm * 128 * mhz * 1e6
 
 
 def _timed(torch, stream, fn, reps):
@@ -63,6 +81,29 @@ def dna2k(ctx, torch, stream, args):
             "gcups": round(len(a) * len(b) / t / 1e9, 2)}
 
 
+def variants(ctx, torch, stream, args):
+    """sw_align of the 2 kbp pair and of the 200 kbp pair with each algorithm of paper Section 2.1."""
+    from .binding import KT_FILL
+    sc = W.dna_scoring()
+    out = {}
+    for name, alg in (("local", 0), ("global", 1), ("semiglobal", 2), ("overlap", 3)):
+        row = {}
+        for tag, (a, b), reps in (("dna2k", W.dna_pair_2k(), REPEATS), ("dna200k", W.dna_long_pair(200_000), 5)):
+            da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+            aln = ctx.align(da, db, sc.matrix, sc.gap_open, sc.gap_extend, algorithm=alg)
+            ctx.timing(True)
+            ts = _timed(torch, stream, lambda: ctx.align(da, db, sc.matrix, sc.gap_open, sc.gap_extend,
+                                                         algorithm=alg), reps)
+            fms, fn = ctx.kernel_time(KT_FILL)
+            ctx.timing(False)
+            t = statistics.median(ts)
+            row[tag] = {"ms": round(1e3 * t, 3), "gcups": round(len(a) * len(b) / t / 1e9, 1),
+                        "fill_gcups": round(len(a) * len(b) / (fms / 1e3 / max(1, fn)) / 1e9, 1),
+                        "score": aln.score, "a": [aln.a_begin, aln.a_end], "b": [aln.b_begin, aln.b_end]}
+        out[name] = row
+    return {"workload": "dna_pairs_by_algorithm", "call": "sw_align", "timing": "CUDA events, median", **out}
+
+
 def dbsearch(ctx, torch, stream, args):
     from .binding import Database
     sc = W.protein_scoring()
@@ -75,21 +116,21 @@ def dbsearch(ctx, torch, stream, args):
     for q in qs:
         db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20)
         ctx.timing(True)
-        ts = _timed(torch, stream, lambda: db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20), 3)
+        ts = _timed(torch, stream, lambda: db.search(q, sc.matrix, sc.gap_open, sc.gap_extend, k=20), REPEATS)
         kms, kn = ctx.kernel_time(KT_DB16)
         ctx.timing(False)
-        t = statistics.median(ts)
+        t, tm = _stats(ts)
         kern_s += kms / 1e3 / max(1, kn)
-        per_query.append({"m": len(q), "ms": round(1e3 * t, 2), "gcups": round(len(q) * total_res / t / 1e9, 1),
-                          "fill_ms": round(kms / max(1, kn), 2)})
+        per_query.append({"m": len(q), "ms": round(1e3 * t, 2), "ms_mean": round(1e3 * tm, 2),
+                          "gcups": round(len(q) * total_res / t / 1e9, 1), "fill_ms": round(kms / max(1, kn), 2)})
     cells = sum(len(q) for q in qs) * total_res
     t_all = sum(x["ms"] for x in per_query) / 1e3
-    peak16 = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6       # two 16-bit lanes per 32-bit lane
+    peak16 = _int_peak(torch) * 2                         # two 16-bit lanes per 32-bit lane
     db.close()
     # the packed fill reads every subject residue once per query sweep (1 B per residue)
     return {"workload": "protein_dbsearch_5q_x_500k", "nseq": pdb.nseq, "residues": total_res,
             "cells": cells, "seconds": round(t_all, 3), "gcups": round(cells / t_all / 1e9, 1),
-            "per_query": per_query,
+            "timing": "CUDA events, median of %d searches per query" % REPEATS, "per_query": per_query,
             "alu_frac_16bit_lanes": round(OPS_PER_CELL * cells / t_all / peak16, 4),
             "fill_hbm_gbs": round(len(qs) * total_res / kern_s / 1e9, 1)}
 
@@ -106,13 +147,10 @@ def batch(ctx, torch, stream, args):
     plan = binding.Batch(ctx, pairs, scorings, flags=binding.SW_BATCH_GRAPH | binding.SW_BATCH_AUTOTUNE,
                          device_inputs=dev)
     plan.run()
-    ts = []
-    for _ in range(5):
-        t0 = time.perf_counter()
-        plan.run()
-        ts.append(time.perf_counter() - t0)
-    t_batch = statistics.median(ts)
+    ts = _timed(torch, stream, plan.run, REPEATS)        # (the plan's own stream, joined by the host copy)
+    t_batch, t_mean = _stats(ts)
     cfg = plan.config()
+    bins = plan.bins()
     plan.close()
     # one sw_score launch per pair, inputs already on the device
     dpairs = []
@@ -125,9 +163,13 @@ def batch(ctx, torch, stream, args):
         ctx.score(a, b, mat, go, ge)
     t_pair = time.perf_counter() - t0
     return {"workload": "batch_10k_uneven_pairs", "cells": cells, "batched_s": round(t_batch, 4),
+            "batched_s_mean": round(t_mean, 4),
             "batched_gcups": round(cells / t_batch / 1e9, 1), "per_pair_s": round(t_pair, 3),
             "per_pair_gcups": round(cells / t_pair / 1e9, 1), "speedup": round(t_pair / t_batch, 2),
-            "tile": {"rows_per_lane": cfg[0], "warps": cfg[1]}, "timing": "wall clock incl. host copy of results"}
+            "tile": {"rows_per_lane": cfg[0], "warps": cfg[1]},
+            "bins": [{"rows_per_lane": r, "warps": w, "lane_bits": lb, "pairs": npr} for r, w, lb, npr in bins],
+            "timing": "CUDA events around each run (its results copied to the host inside), median of %d; "
+                      "per pair: one pass of 10,000 sw_score calls, wall clock" % REPEATS}
 
 
 def serve(ctx, torch, stream, args):
@@ -180,9 +222,12 @@ def serve(ctx, torch, stream, args):
                     "p99_s": round(float(np.percentile(lat, 99)), 3), "sustained_gcups": round(cells / wall / 1e9, 1),
                     "busy_gcups": round(cells / busy / 1e9, 1), "steps": steps, "deferred_submits": deferred,
                     "offered_gcups": round(rate * cells / len(reqs) / 1e9, 1)})
+        # the device's capacity is its busy-time throughput: above it the queue grows
+        out[-1]["load"] = "overload" if out[-1]["offered_gcups"] > out[-1]["busy_gcups"] else "below capacity"
     db.close()
     return {"workload": "serving_poisson_protein_vs_500k", "chunks": 8, "max_slots": 64, "k": 20,
-            "note": "offered load exceeds device capacity at every rate; latency is queue-dominated",
+            "note": "load = offered GCUPS (rate x mean cells per request) against the busy-time GCUPS; under "
+                    "overload latency is queue-dominated",
             "rates": out}
 
 
@@ -213,7 +258,8 @@ def run_all(names, args):
     ctx = Context(0, stream)
     res = {}
     for nm in names:
-        fn = {"dna2k": dna2k, "dbsearch": dbsearch, "batch": batch, "serve": serve, "dna5m": dna5m}[nm]
+        fn = {"dna2k": dna2k, "variants": variants, "dbsearch": dbsearch, "batch": batch, "serve": serve,
+              "dna5m": dna5m}[nm]
         t0 = time.perf_counter()
         try:
             res[nm] = fn(ctx, torch, stream, args)

@@ -93,6 +93,9 @@ def load():
     lib.sw_batch_destroy.argtypes = [vp]
     lib.sw_batch_destroy.restype = None
     lib.sw_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.sw_batch_bin_config.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64)]
     lib.sw_score_batch.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
     lib.sw_server_create.argtypes = [vp, vp, ctypes.POINTER(_Scoring), ctypes.c_size_t, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
@@ -300,6 +303,18 @@ class Batch:
         _check(self._lib.sw_batch_config(self.handle, ctypes.byref(r), ctypes.byref(w)), "sw_batch_config")
         return r.value, w.value
 
+    def bins(self):
+        """Per bin: (rows per lane, warps, lane bits, pairs), largest bin first."""
+        out = []
+        while True:
+            r, w, lb, npr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+            rc = self._lib.sw_batch_bin_config(self.handle, len(out), ctypes.byref(r), ctypes.byref(w),
+                                               ctypes.byref(lb), ctypes.byref(npr))
+            if rc == SW_ERANGE:
+                return out
+            _check(rc, "sw_batch_bin_config")
+            out.append((r.value, w.value, lb.value, npr.value))
+
     def run(self):
         _check(self._lib.sw_batch_run(self.handle, self._out), "sw_batch_run")
         return [Hit(h.score, h.a_end, h.b_end) for h in self._out[:self.npairs]]
@@ -426,7 +441,8 @@ class Server:
 
 
 PROBE_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,
-             "viaddmax_s16x2": 4, "vimax3_s16x2_relu": 5, "prmt": 6, "shfl": 7}
+             "viaddmax_s16x2": 4, "vimax3_s16x2_relu": 5, "prmt": 6, "shfl": 7,
+             "vaddus4": 8, "vsubus4": 9, "vmaxu4": 10}
 
 
 def probe_int_rates(ctx: Context, iters: int = 2000) -> dict:

@@ -134,13 +134,22 @@ __device__ __forceinline__ unsigned merge_row(const uint32_t *wa, const uint32_t
     }
 }
 
+// Profile bytes a lane owns per pass: its R rows rounded up to whole 32-bit
+// words, so that every lane's profile load is aligned (R = 5 or 6 gives
+// 160- or 192-row passes, which pad a short query far less than 256).
+constexpr int db_lane_slot(int R) { return ((R + 3) / 4) * 4; }
+
 template <int R>
-__device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R / 4]) {
-    if constexpr (R == 4) {
+__device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[db_lane_slot(R) / 4]) {
+    constexpr int LS = db_lane_slot(R);
+    if constexpr (LS == 4) {
         w[0] = *reinterpret_cast<const uint32_t *>(p);
-    } else if constexpr (R == 8) {
+    } else if constexpr (LS == 8) {
         const uint2 v = *reinterpret_cast<const uint2 *>(p);
         w[0] = v.x; w[1] = v.y;
+    } else if constexpr (LS == 12) {             // 12-byte lane slots: 4-byte aligned only
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(p);
+        w[0] = q[0]; w[1] = q[1]; w[2] = q[2];
     } else {
         const uint4 v = *reinterpret_cast<const uint4 *>(p);
         w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
@@ -150,7 +159,7 @@ __device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[R
 // grid: 1D; blocks [jobs[j].block0, jobs[j+1].block0) work on job j (the
 // host gives each job blocks in proportion to its work); block: W warps.
 // Dynamic shared memory: the query profile, (K + 1) * mpad bytes,
-// mpad = passes * 32 * R.
+// mpad = passes * 32 * db_lane_slot(R) (lane slots of whole words).
 constexpr int kDbCH = 8;      // steps per chunk of the packed fill (steady chunks skip all range tests)
 
 // Per-lane state of the packed fill: U = H - open and E of the lane's R query
@@ -189,7 +198,7 @@ __device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, c
         if (tops) topn = bnd[s + 1];                    // s + 1 <= n: inside the scratch row
     }
     if (!CHECK || (j >= 0 && j < n)) {
-        uint32_t wa[R / 4], wb[R / 4];
+        uint32_t wa[db_lane_slot(R) / 4], wb[db_lane_slot(R) / 4];
         load_prof_words<R>(st.prow + min((int)(st.cp & 0xffu), K) * mpad, wa);
         load_prof_words<R>(st.prow + min((int)(st.cp >> 8), K) * mpad, wb);
         unsigned udiag = st.udiag0;
@@ -212,6 +221,7 @@ __device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, c
         st.fb = f;
 #pragma unroll
         for (int r = 0; r + 1 < R; r += 2) st.cmax = __vimax3_s16x2(st.cmax, st.U[r], st.U[r + 1]);
+        if constexpr (R % 2 == 1) st.cmax = __vimax3_s16x2(st.cmax, st.U[R - 1], st.U[R - 1]);
         if (!last && lane == 31) bnd[j] = make_uint2(st.ub, st.fb);
     }
     st.cp = cpn;
@@ -219,7 +229,7 @@ __device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, c
 }
 
 template <int R, int W, bool OVERSUB>
-__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : (R >= 16 ? 3 : 4))
+__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : (R >= 12 ? 3 : 4))
 db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                 const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {
@@ -244,11 +254,13 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
     const int K = SC.K, go = SC.go, ge = SC.ge;
     const int m = J.m;
     constexpr int ROWS = 32 * R;
+    constexpr int LS = db_lane_slot(R), PROWS = 32 * LS;   // profile bytes per lane and per pass
     const int passes = (m + ROWS - 1) / ROWS;
-    const int mpad = passes * ROWS;
+    const int mpad = passes * PROWS;
     for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
-        const bool ok = i < m;
-        const int qc = ok ? min((int)J.q[i], K - 1) : 0;
+        const int r = i % LS, row = (i / PROWS) * ROWS + ((i % PROWS) / LS) * R + r;
+        const bool ok = r < R && row < m;
+        const int qc = ok ? min((int)J.q[row], K - 1) : 0;
         for (int c = 0; c <= K; ++c)
             prof[c * mpad + i] = (ok && c < K) ? (int8_t)(SC.mat[qc * K + c] + go) : (int8_t)kPadScore;
     }
@@ -274,7 +286,7 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
         unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
         for (int pass = 0; pass < passes; ++pass) {
             DbLane<R> st;
-            st.prow = prof + pass * ROWS + lane * R;
+            st.prow = prof + pass * PROWS + lane * LS;
 #pragma unroll
             for (int r = 0; r < R; ++r) { st.U[r] = ngo2; st.E[r] = neg2; }
             st.ub = ngo2; st.fb = neg2; st.udiag0 = ngo2;

@@ -63,10 +63,14 @@ int launch_v_mode(sw_ctx *c, int mode, bool fold, const FillLaunch &L, int K, lo
 
 }  // namespace
 
-// Eight rows a lane where the strips fit the SMs once, else sixteen.
+// The fewest rows a lane (8, 12 or 16) that give at most one strip per SM,
+// as for the local fill: the strips of a pair form one chain.
 FillConfig swgb::variant_fill_config(const sw_ctx *c, int64_t rows) {
-    const int64_t sh = 4LL * 32 * 8;
-    const int R = (rows + sh - 1) / sh <= (int64_t)c->nsm ? 8 : 16;
+    int R = 16;
+    for (int r : {8, 12}) {
+        const int64_t sh = 4LL * 32 * r;
+        if ((rows + sh - 1) / sh <= (int64_t)c->nsm) { R = r; break; }
+    }
     FillConfig f{R, 4, 0, 2};
     f.alg = 1;
     return f;
@@ -78,6 +82,7 @@ int swgb::launch_fill_variant(sw_ctx *c, const FillConfig &cfg, int mode, bool f
     if (cfg.W != 4) return SW_EINVAL;
     switch (cfg.R) {
         case 8: return launch_v_mode<8>(c, mode, fold, L, K, tickets, cfg.B);
+        case 12: return launch_v_mode<12>(c, mode, fold, L, K, tickets, cfg.B);
         case 16: return launch_v_mode<16>(c, mode, fold, L, K, tickets, cfg.B);
         default: return SW_EINVAL;
     }

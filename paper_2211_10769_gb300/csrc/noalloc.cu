@@ -12,10 +12,14 @@
 // kNoAllocScratchBytes.  Each GPU that loads the library holds that array
 // until the process exits.
 //
-// The array's name is only a host-side stand-in in host code, so the first
-// call on each device (with that device current) looks up its device
-// address with cudaGetSymbolAddress and caches it; that first call should
-// come before any stream capture.  Every call shares the array and it keeps
+// The array's name is only a host-side stand-in in host code, so every call
+// looks up its device address with cudaGetSymbolAddress in the current
+// context (and sets the fill's shared-memory limit there).  Nothing is
+// cached across calls: a device reset (cudaDeviceReset) or a new primary
+// context reloads the module, possibly at another address, and a cached
+// address would then point at freed memory.  The first call in a context
+// loads the module and should come before any stream capture; later
+// lookups are host-side table reads.  Every call shares the array and it keeps
 // the previous call's contents, so each call clears the counters that must
 // start at zero; calls whose work overlaps on the GPU (different streams,
 // or host threads racing) would race on the array and must be serialised
@@ -27,7 +31,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 using namespace swgb;
 
@@ -51,29 +54,21 @@ static_assert(sizeof(FillTask) <= 256, "task record must fit its slot");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
-
-// Once per device: device address of the scratch array and the fill's
-// shared-memory limit.  Runs with `dev` current.
-int setup_device(int dev, unsigned char **out) {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return SW_ECUDA;
-        }
-        if (cudaFuncSetAttribute(wavefront_kernel<kR, kW, kModeScore, kProf8>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (kMaxAlphabet + 1) * kHC) != cudaSuccess) {
-            cudaGetLastError();
-            return SW_ECUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+// Device address of the scratch array in the current context, and the
+// fill's shared-memory limit there.
+int setup_device(unsigned char **out) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return SW_ECUDA;
     }
-    *out = g_scratch_ptr[dev];
+    if (cudaFuncSetAttribute(wavefront_kernel<kR, kW, kModeScore, kProf8>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (kMaxAlphabet + 1) * kHC) != cudaSuccess) {
+        cudaGetLastError();
+        return SW_ECUDA;
+    }
+    *out = static_cast<unsigned char *>(p);
     return SW_OK;
 }
 
@@ -96,9 +91,8 @@ extern "C" int sw_score_noalloc(void *cuda_stream, const uint8_t *a, int64_t m, 
     if (!is_device_ptr(a) || !is_device_ptr(b)) return SW_EINVAL;   // inputs must already be on the device
     int dev = 0;
     CU(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return SW_EINVAL;
     unsigned char *base = nullptr;
-    rc = setup_device(dev, &base);
+    rc = setup_device(&base);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 

@@ -25,6 +25,9 @@ __device__ __forceinline__ unsigned step(unsigned x, unsigned y, unsigned z, uns
     else if constexpr (OP == SW_PROBE_VIADDMAX_S16X2) return __viaddmax_s16x2(x, c, y);
     else if constexpr (OP == SW_PROBE_VIMAX3_S16X2_RELU) return __vimax3_s16x2_relu(x, y, z);
     else if constexpr (OP == SW_PROBE_PRMT) return __byte_perm(x, y, c);
+    else if constexpr (OP == SW_PROBE_VADDUS4) return __vaddus4(x, y);
+    else if constexpr (OP == SW_PROBE_VSUBUS4) return __vsubus4(x, y);
+    else if constexpr (OP == SW_PROBE_VMAXU4) return __vmaxu4(x, y);
     else return x ^ __shfl_xor_sync(0xffffffffu, y, 1);
 }
 
@@ -135,6 +138,9 @@ extern "C" int sw_probe_latency(sw_ctx *c, int op, int iters, double *cycles) {
         case SW_PROBE_VIMAX3_S16X2_RELU: return run_latency<SW_PROBE_VIMAX3_S16X2_RELU>(c, iters, cycles);
         case SW_PROBE_PRMT: return run_latency<SW_PROBE_PRMT>(c, iters, cycles);
         case SW_PROBE_SHFL: return run_latency<SW_PROBE_SHFL>(c, iters, cycles);
+        case SW_PROBE_VADDUS4: return run_latency<SW_PROBE_VADDUS4>(c, iters, cycles);
+        case SW_PROBE_VSUBUS4: return run_latency<SW_PROBE_VSUBUS4>(c, iters, cycles);
+        case SW_PROBE_VMAXU4: return run_latency<SW_PROBE_VMAXU4>(c, iters, cycles);
         default: return SW_EINVAL;
     }
 }
@@ -151,6 +157,9 @@ extern "C" int sw_probe_int_rate(sw_ctx *c, int op, int iters, double *per_sm_pe
         case SW_PROBE_VIMAX3_S16X2_RELU: return run<SW_PROBE_VIMAX3_S16X2_RELU>(c, iters, per_sm_per_clk, sm_mhz);
         case SW_PROBE_PRMT: return run<SW_PROBE_PRMT>(c, iters, per_sm_per_clk, sm_mhz);
         case SW_PROBE_SHFL: return run<SW_PROBE_SHFL>(c, iters, per_sm_per_clk, sm_mhz);
+        case SW_PROBE_VADDUS4: return run<SW_PROBE_VADDUS4>(c, iters, per_sm_per_clk, sm_mhz);
+        case SW_PROBE_VSUBUS4: return run<SW_PROBE_VSUBUS4>(c, iters, per_sm_per_clk, sm_mhz);
+        case SW_PROBE_VMAXU4: return run<SW_PROBE_VMAXU4>(c, iters, per_sm_per_clk, sm_mhz);
         default: return SW_EINVAL;
     }
 }

@@ -257,7 +257,11 @@ FillConfig swgb::pair_fill_config(const sw_ctx *c, int64_t rows) {
 // fewest rows per lane in {8, 12, 16} that give at most one strip per SM;
 // else the int32 fill of pair_fill_config.
 FillConfig swgb::pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevScoring &s) {
-    if (s.alg != kAlgLocal) return variant_fill_config(c, rows);
+    if (s.alg != kAlgLocal) {
+        FillConfig f = variant_fill_config(c, rows);
+        if (!c->fwd_auto && (c->fwd.R == 8 || c->fwd.R == 12 || c->fwd.R == 16)) f.R = c->fwd.R;   // SWGB_FWD
+        return f;
+    }
     if (!c->fwd_auto) {
         FillConfig f = c->fwd;
         f.P16 = f.P16 && p16_fits(s, f.R) && f.W == 4;
@@ -417,14 +421,16 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     c->fwd = FillConfig{8, 4, 0, 2};
     c->tbc = FillConfig{8, 4};
     c->bat = FillConfig{8, 4};
-    // tuning overrides: SWGB_FWD="R,W[,S[,B]]", SWGB_TB="R,W" and SWGB_BATCH="R,W" (tile shapes of the fills)
+    // tuning overrides: SWGB_FWD="R,W[,S[,B[,P16]]]", SWGB_TB="R,W" and SWGB_BATCH="R,W[,P16]" (tile shapes
+    // and lane widths of the fills)
     if (const char *f = std::getenv("SWGB_FWD")) {
         std::sscanf(f, "%d,%d,%d,%d,%d", &c->fwd.R, &c->fwd.W, &c->fwd.S, &c->fwd.B, &c->fwd.P16);
         c->fwd_auto = false;
     }
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
-    if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d", &c->bat.R, &c->bat.W);
+    if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d,%d", &c->bat.R, &c->bat.W, &c->bat.P16);
     if (const char *f = std::getenv("SWGB_PROF32")) c->prof32 = std::atoi(f) != 0;
+    if (const char *f = std::getenv("SWGB_ONE_ROUND")) c->one_round = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_P16")) c->p16 = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_PACE")) c->pace_permille = std::max(0, std::atoi(f));
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);

@@ -84,6 +84,29 @@ int border_alignment(int alg, int score, int64_t ie, int64_t je, sw_alignment *o
     return SW_OK;
 }
 
+// The alignment from the walk's run records (stored end -> start), after the
+// forced run of a path that reached the border (the global and semi-global
+// algorithms).
+int finish_alignment(int alg, int score, int64_t ie, int64_t je, const WalkState &w, const int2 *runs,
+                     sw_alignment *out) {
+    int64_t bi = w.i, bj = w.j;
+    std::string cig = border_run(alg, &bi, &bj);
+    cig.reserve(cig.size() + (size_t)w.nruns * 6);
+    static const char opc[3] = {'M', 'I', 'D'};
+    char buf[24];
+    for (long long k = w.nruns - 1; k >= 0; --k) {
+        const int2 r = runs[(size_t)k];
+        if (r.x < 0 || r.x > 2) return SW_ECUDA;
+        std::snprintf(buf, sizeof(buf), "%d%c", r.y, opc[r.x]);
+        cig += buf;
+    }
+    char *s = static_cast<char *>(std::malloc(cig.size() + 1));
+    if (!s) return SW_ENOMEM;
+    std::memcpy(s, cig.c_str(), cig.size() + 1);
+    *out = sw_alignment{score, 0, bi, ie, bj, je, s, (int64_t)cig.size()};
+    return SW_OK;
+}
+
 template <typename Word, int R>
 int launch_walk_t(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int nJ, int BT) {
     if ((long long)nI * nJ > kWalkTableMax || BT < kWalkMinBT || BT % R != 0) return SW_EINVAL;
@@ -115,6 +138,128 @@ int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int
     }
 }
 
+// Sides up to this many cells take the one-round reconstruction below.
+constexpr int64_t kOneRoundSide = 8192;
+
+// Reconstruction of a small pair in one round, with one host synchronisation:
+// the score fill (end-cell candidates) and a traceback fill of the whole
+// matrix as a single BT x BT tile, the end cell reduced on the device, the walk
+// started from it there (walk_start_kernel), and every result copied back at
+// once.  The decision bits of the whole matrix cost BT * BT / 2 bytes (32 MB at
+// the largest side); in exchange there are no checkpoints, no bands and no
+// host round trips between the steps, which dominate small pairs.
+int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, int64_t n, const DevScoring &ds,
+                    bool fold, sw_alignment *out) {
+    const FillConfig fwd = pair_fill_config_for(c, m, ds);
+    const int sw = pair_strip_warps(c, fwd, m);
+    const int HC = sw * 32 * fwd.R;
+    FillConfig tbc = c->tbc;
+    tbc.P16 = 0;
+    tbc.alg = ds.alg;
+    if (ds.alg != kAlgLocal && tbc.R != 8 && tbc.R != 12 && tbc.R != 16) tbc.R = 8;
+    const int R = tbc.R;
+    const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
+    const int HS = tsw * 32 * R;
+    // one tile holds the whole matrix: its side is a multiple of R and of 64, at least kWalkMinBT
+    long long BT = std::max<long long>(std::max(m, n), kWalkMinBT);
+    BT = (BT + 63) / 64 * 64;
+    BT = (BT + R - 1) / R * R;
+    const size_t tile_bytes = (size_t)((BT + R - 1) / R) * (size_t)BT * (size_t)tb_word_bytes(R);
+
+    FillTask t{};                                   // the score fill
+    t.a = da; t.b = db;
+    t.rows = (int32_t)m; t.ncols = (int32_t)n;
+    t.strip_warps = sw;
+    t.nstrips = (int32_t)((m + HC - 1) / HC);
+    t.nslot = std::min(t.nstrips, 4);
+    FillTask u{};                                   // the traceback fill, one tile
+    u.a = da; u.b = db;
+    u.rows = (int32_t)m; u.ncols = (int32_t)n;
+    u.strip_warps = tsw;
+    u.nstrips = (int32_t)((m + HS - 1) / HS);
+    u.nslot = std::min(u.nstrips, 4);
+    u.tb_ld = BT;
+    RC(c->bnd.ensure((size_t)(t.nslot + u.nslot) * (size_t)n * sizeof(int2)));
+    t.bnd = static_cast<int2 *>(c->bnd.p);
+    u.bnd = t.bnd + (size_t)t.nslot * (size_t)n;
+    RC(c->tb.ensure(tile_bytes));
+    u.tb = c->tb.p;
+    const long long tickets = (long long)t.nstrips + u.nstrips;
+    RC(c->tasks.ensure(2 * sizeof(FillTask)));
+    RC(c->prog.ensure((size_t)tickets * sizeof(int)));
+    RC(c->cand.ensure((size_t)tickets * sizeof(int4)));
+    RC(c->ticket.ensure(2 * sizeof(unsigned long long)));
+    RC(c->result.ensure(sizeof(int4)));
+    RC(c->walk.ensure(sizeof(WalkState)));
+    RC(c->runs.ensure((size_t)(m + n + 2) * sizeof(int2)));
+    RC(c->misc.ensure(sizeof(void *)));
+    // host staging: the two tasks and the one-entry tile table go down in two copies
+    const size_t tab_off = (2 * sizeof(FillTask) + 15) / 16 * 16;
+    RC(c->stage.ensure(tab_off + sizeof(void *)));
+    std::memcpy(c->stage.p, &t, sizeof(t));
+    std::memcpy(static_cast<char *>(c->stage.p) + sizeof(FillTask), &u, sizeof(u));
+    const void *tile = c->tb.p;
+    std::memcpy(static_cast<char *>(c->stage.p) + tab_off, &tile, sizeof(tile));
+    CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, 2 * sizeof(FillTask), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->misc.p, static_cast<char *>(c->stage.p) + tab_off, sizeof(void *),
+                       cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->prog.p, 0, (size_t)tickets * sizeof(int), c->stream));
+    CU(cudaMemsetAsync(c->ticket.p, 0, 2 * sizeof(unsigned long long), c->stream));
+
+    const FillTask *dtasks = static_cast<const FillTask *>(c->tasks.p);
+    FillLaunch L{};
+    L.tasks = dtasks;
+    L.scorings = static_cast<const DevScoring *>(c->scorings.p);
+    L.ticket = static_cast<unsigned long long *>(c->ticket.p);
+    L.prog = static_cast<int *>(c->prog.p);
+    L.cand = static_cast<int4 *>(c->cand.p);
+    L.err = static_cast<int *>(c->err.p);
+    L.total = t.nstrips;
+    L.spin_limit = c->spin_limit;
+    L.ntasks = 1;
+    L.pace_permille = c->pace_permille;
+    RC(launch_fill(c, fwd, kModeScore, fold, L, ds.K, t.nstrips));
+    reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(dtasks, 1, static_cast<const int4 *>(c->cand.p),
+                                                       static_cast<const DevScoring *>(c->scorings.p),
+                                                       static_cast<int4 *>(c->result.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    FillLaunch Lt = L;                              // the traceback fill: its own tickets and progress
+    Lt.tasks = dtasks + 1;
+    Lt.ticket = static_cast<unsigned long long *>(c->ticket.p) + 1;
+    Lt.prog = static_cast<int *>(c->prog.p) + t.nstrips;
+    Lt.cand = static_cast<int4 *>(c->cand.p) + t.nstrips;
+    Lt.total = u.nstrips;
+    RC(launch_fill(c, tbc, kModeTb, fold, Lt, ds.K, u.nstrips));
+    walk_start_kernel<<<1, 32, 0, c->stream>>>(static_cast<const int4 *>(c->result.p), ds.alg == kAlgLocal ? 1 : 0,
+                                               static_cast<WalkState *>(c->walk.p));
+    CU(cudaGetLastError());
+    ++c->launches;
+    RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), 0, 0, 1, 1, (int)BT, R));
+
+    // everything back at once: end cell, walk state, error word, run records
+    const size_t runs_off = 128;
+    const size_t runs_bytes = (size_t)(m + n + 2) * sizeof(int2);
+    RC(c->stage3.ensure(runs_off + runs_bytes));
+    char *h = static_cast<char *>(c->stage3.p);
+    CU(cudaMemcpyAsync(h, c->result.p, sizeof(int4), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(h + 16, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(h + 32, c->walk.p, sizeof(WalkState), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(h + runs_off, c->runs.p, runs_bytes, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    int4 res;
+    int e;
+    WalkState w;
+    std::memcpy(&res, h, sizeof(int4));
+    std::memcpy(&e, h + 16, sizeof(int));
+    std::memcpy(&w, h + 32, sizeof(WalkState));
+    RC(map_kernel_error(e));
+    if (ds.alg == kAlgLocal && res.x <= 0) return empty_alignment(out);
+    if (res.y == 0 || res.z == 0) return border_alignment(ds.alg, res.x, res.y, res.z, out);
+    if (w.done != 1 || w.nruns < 0 || w.nruns > m + n) return SW_ECUDA;   // one tile holds every cell
+    return finish_alignment(ds.alg, res.x, res.y, res.z, w, reinterpret_cast<const int2 *>(h + runs_off), out);
+}
+
 }  // namespace
 
 extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
@@ -140,6 +285,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
     const bool fold = fold_open(ds);
+    if (c->one_round && std::max(m, n) <= kOneRoundSide) return align_one_round(c, da, m, db, n, ds, fold, out);
 
     // ---- tile side: both checkpoint sets within the budget
     // tiles are BT x BT; BT is a multiple of both fills' strip heights, so
@@ -290,26 +436,10 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     }
     if (w.done != 1) return SW_ECUDA;     // the walk must end at a zero cell or the border
 
-    // ---- 4. CIGAR text from the run records (stored end -> start), after the forced run of a
-    // path that reached the border (the global and semi-global algorithms)
+    // ---- 4. CIGAR text from the run records
     std::vector<int2> runs((size_t)w.nruns);
     if (w.nruns > 0) {
         CU(cudaMemcpy(runs.data(), c->runs.p, (size_t)w.nruns * sizeof(int2), cudaMemcpyDeviceToHost));
     }
-    int64_t bi = w.i, bj = w.j;
-    std::string cig = border_run(ds.alg, &bi, &bj);
-    cig.reserve(cig.size() + (size_t)w.nruns * 6);
-    static const char opc[3] = {'M', 'I', 'D'};
-    char buf[24];
-    for (long long k = w.nruns - 1; k >= 0; --k) {
-        const int2 r = runs[(size_t)k];
-        if (r.x < 0 || r.x > 2) return SW_ECUDA;
-        std::snprintf(buf, sizeof(buf), "%d%c", r.y, opc[r.x]);
-        cig += buf;
-    }
-    char *s = static_cast<char *>(std::malloc(cig.size() + 1));
-    if (!s) return SW_ENOMEM;
-    std::memcpy(s, cig.c_str(), cig.size() + 1);
-    *out = sw_alignment{res.x, 0, bi, (int64_t)ie, bj, (int64_t)je, s, (int64_t)cig.size()};
-    return SW_OK;
+    return finish_alignment(ds.alg, res.x, ie, je, w, runs.data(), out);
 }

@@ -12,7 +12,10 @@
 // the scatter of results back to pair order, the copy to the host) can be
 // captured once in a CUDA graph and replayed.  Each bin's tile shape is
 // picked from a candidate set by timing the plan itself (autotuning), and
-// the choice is cached in the context for bins of the same size class.
+// the choice is cached in the context for bins of the same size class.  The
+// candidates include the packed 16-bit fill (wavefront16.cuh) wherever its
+// exactness test passes for the bin's scoring scheme, so the autotuner
+// chooses the lane width as well as the tile shape.
 #include "sw.h"
 #include "sw_ctx.h"
 #include "wavefront.cuh"
@@ -50,7 +53,8 @@ static __global__ void scatter_hits_kernel(const int4 *res, const int32_t *pair,
     if (k < ntasks) out[pair[k]] = res[k];
 }
 
-const FillConfig kCandidates[] = {{8, 4}, {4, 4}, {12, 4}, {16, 4}, {8, 8}};
+const FillConfig kCandidates[] = {{8, 4}, {4, 4}, {12, 4}, {16, 4}, {8, 8},
+                                  {8, 4, 0, 0, 1}, {12, 4, 0, 0, 1}, {16, 4, 0, 0, 1}};
 
 constexpr int64_t kShortRows = 1024;      // row classes: queries up to this many rows, and longer
 
@@ -370,6 +374,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
         std::stable_sort(bins.begin(), bins.end(), [&](const Bin &x, const Bin &y) { return bin_cells(x) > bin_cells(y); });
         for (Bin &bin : bins) {
             bin.cfg = c->bat;
+            if (bin.cfg.P16 && (bin.cfg.W != 4 || !p16_fits(B->scorings[(size_t)bin.sidx], bin.cfg.R))) bin.cfg.P16 = 0;
             if (B->scorings[(size_t)bin.sidx].alg != kAlgLocal) {   // global, semi-global, overlap
                 bin.cfg = FillConfig{bin.rclass ? 16 : 8, 4};
                 bin.cfg.alg = 1;
@@ -407,6 +412,7 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
             float best = 1e30f;
             FillConfig pick = B->bins[k].cfg;
             for (const FillConfig &cand : kCandidates) {
+                if (cand.P16 && !p16_fits(B->scorings[(size_t)B->bins[k].sidx], cand.R)) continue;
                 B->bins[k].cfg = cand;
                 rc = build_plan(B);
                 if (!rc) rc = cudaEventRecord(e0, B->stream) == cudaSuccess ? SW_OK : SW_ECUDA;
@@ -468,6 +474,18 @@ extern "C" int sw_batch_config(const sw_batch *B, int32_t *rows_per_lane, int32_
     if (!B || !rows_per_lane || !warps) return SW_EINVAL;
     *rows_per_lane = B->cfg.R;
     *warps = B->cfg.W;
+    return SW_OK;
+}
+
+extern "C" int sw_batch_bin_config(const sw_batch *B, int32_t bin, int32_t *rows_per_lane, int32_t *warps,
+                                   int32_t *lane_bits, int64_t *npairs) {
+    if (!B || !rows_per_lane || !warps || !lane_bits || !npairs || bin < 0) return SW_EINVAL;
+    if ((size_t)bin >= B->bins.size()) return SW_ERANGE;
+    const Bin &b = B->bins[(size_t)bin];
+    *rows_per_lane = b.cfg.R;
+    *warps = b.cfg.W;
+    *lane_bits = b.cfg.P16 ? 16 : 32;
+    *npairs = (int64_t)b.pairs.size();
     return SW_OK;
 }
 

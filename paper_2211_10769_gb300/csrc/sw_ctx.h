@@ -75,8 +75,9 @@ struct sw_ctx {
     swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
     bool prof32 = true;               // int32 query profiles where they fit (small alphabets)
     bool p16 = true;                  // packed 16-bit pair fill where it is exact (p16_fits)
-    int pace_permille = 20;           // slow-down of a strip chain's first warp (FillLaunch)
+    int pace_permille = 0;            // slow-down of a strip chain's first warp (FillLaunch; off: measured no gain)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
+    bool one_round = false;           // sw_align of small pairs in one round (whole-matrix traceback bits)
     int tb_strip_warps = 0;           // compute warps per traceback strip (0 = all)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
@@ -126,7 +127,11 @@ int db_score_all(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const
 int db_rescore(sw_ctx *c, const sw_db *db, const uint8_t *dq, int64_t m, const DevScoring &ds,
                const std::vector<int32_t> &flagged, int32_t *dscores);
 int db_topk(sw_ctx *c, const int32_t *dscores, int64_t nseq, int k, int2 *dout);
-int db_shape(int K, int m);
+int db_shape(int K, int m);                // tile shape (index) for a query of m residues
+int db_shape_warps(int shape);
+int db_shape_rows(int shape);              // query rows per pass
+int db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out);
+int db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m);
 int db_resident_blocks(sw_ctx *c, int K, int m, int *out);
 int db_warps_per_block(int K, int m);
 int db_rows_per_pass(int K, int m);      // query rows per pass of the packed kernel for this launch shape

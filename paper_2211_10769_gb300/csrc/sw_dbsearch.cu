@@ -41,11 +41,18 @@ static __global__ void max_code_kernel(const uint8_t *s, long long len, int *out
 
 constexpr long long kMaxProfileSmem = 200 * 1024;
 
+// Profile bytes of a query of m residues for tile shape R (whole passes of
+// 32 lane slots of db_lane_slot(R) bytes, per residue code and padding).
+template <int R>
+size_t db_profile_bytes(int K, int m) {
+    constexpr int ROWS = 32 * R;
+    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * 32 * db_lane_slot(R);
+    return (size_t)(K + 1) * (size_t)mpad;
+}
+
 template <int R, int W>
 int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m) {
-    constexpr int ROWS = 32 * R;
-    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
-    const size_t smem = (size_t)(K + 1) * (size_t)mpad;
+    const size_t smem = db_profile_bytes<R>(K, m);
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false>, W * 32, smem));
     int occ2 = 0;
@@ -81,9 +88,7 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
 
 template <int R, int W>
 int resident_blocks(sw_ctx *c, int K, int m, int *out) {
-    constexpr int ROWS = 32 * R;
-    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * ROWS;
-    const size_t smem = (size_t)(K + 1) * (size_t)mpad;
+    const size_t smem = db_profile_bytes<R>(K, m);
     if ((long long)smem > kMaxProfileSmem) return SW_ERANGE;
     static int attr_set[64] = {0};
     if (c->device < 64 && !attr_set[c->device]) {
@@ -100,36 +105,82 @@ int resident_blocks(sw_ctx *c, int K, int m, int *out) {
     return SW_OK;
 }
 
-// Tile shape by query length: the whole profile must sit in shared memory;
-// long queries use one block of 32 warps per SM.
+// Tile shapes of the packed search: rows a lane and warps a block.  A query
+// is padded to whole passes of 32 R rows, so short queries want small R
+// (144 residues: one 160-row pass at R = 5 instead of 256 rows at R = 8);
+// long ones want R = 16, whose per-step overhead is shared by more rows.
+// Queries whose profile would not leave room for three blocks an SM take
+// blocks of 32 warps (one per SM) at R = 8.
+struct DbShape { int R, W; };
+constexpr DbShape kDbShapes[] = {{4, 8}, {5, 8}, {6, 8}, {8, 8}, {12, 8}, {16, 8}, {8, 32}};
+constexpr int kDbWide = 6;                         // index of the 32-warp shape
+constexpr size_t kDbNarrowProfileMax = 96 * 1024;  // profile bytes of a three-blocks-an-SM shape at most
+
+size_t shape_profile_bytes(int s, int K, int m) {
+    switch (kDbShapes[s].R) {
+        case 4: return db_profile_bytes<4>(K, m);
+        case 5: return db_profile_bytes<5>(K, m);
+        case 6: return db_profile_bytes<6>(K, m);
+        case 12: return db_profile_bytes<12>(K, m);
+        case 16: return db_profile_bytes<16>(K, m);
+        default: return db_profile_bytes<8>(K, m);
+    }
+}
+
 }  // namespace
 
-// Tile shape by the longest query of the launch: the whole profile must sit
-// in shared memory; long queries use one block of 32 warps per SM.
+// The shape for a query of m residues: the least padded work, counting the
+// per-step overhead of a lane (about 1.5 rows' worth) and a pass boundary
+// (about 16 rows), among the shapes whose profile fits.
 int swgb::db_shape(int K, int m) {
-    const long long prof8 = (long long)(K + 1) * (((m + 255) / 256) * 256);
-    if (prof8 > 96 * 1024) return 2;
-    return m > 256 ? 1 : 0;                 // 16 rows a lane once a query fills more than one 256-row pass
+    int best = kDbWide;
+    double best_cost = 1e300;
+    for (int s = 0; s < kDbWide; ++s) {
+        if (shape_profile_bytes(s, K, m) > kDbNarrowProfileMax) continue;
+        const int R = kDbShapes[s].R, rows = 32 * R;
+        const long long passes = (m + rows - 1) / rows;
+        const double cost = (double)passes * rows * (R + 1.5) / R + 16.0 * (double)passes;
+        if (cost < best_cost) { best_cost = cost; best = s; }
+    }
+    return best;
+}
+
+int swgb::db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out) {
+    switch (shape) {
+        case 0: return resident_blocks<4, 8>(c, K, m, out);
+        case 1: return resident_blocks<5, 8>(c, K, m, out);
+        case 2: return resident_blocks<6, 8>(c, K, m, out);
+        case 3: return resident_blocks<8, 8>(c, K, m, out);
+        case 4: return resident_blocks<12, 8>(c, K, m, out);
+        case 5: return resident_blocks<16, 8>(c, K, m, out);
+        default: return resident_blocks<8, 32>(c, K, m, out);
+    }
 }
 
 int swgb::db_resident_blocks(sw_ctx *c, int K, int m, int *out) {
-    switch (db_shape(K, m)) {
-        case 2: return resident_blocks<8, 32>(c, K, m, out);
-        case 1: return resident_blocks<16, 8>(c, K, m, out);
-        default: return resident_blocks<8, 8>(c, K, m, out);
+    return db_resident_blocks_shape(c, db_shape(K, m), K, m, out);
+}
+
+int swgb::db_shape_warps(int shape) { return kDbShapes[shape].W; }
+int swgb::db_shape_rows(int shape) { return 32 * kDbShapes[shape].R; }
+int swgb::db_warps_per_block(int K, int m) { return db_shape_warps(db_shape(K, m)); }
+int swgb::db_rows_per_pass(int K, int m) { return db_shape_rows(db_shape(K, m)); }
+
+int swgb::db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K,
+                          int m) {
+    switch (shape) {
+        case 0: return launch_db<4, 8>(c, jobs, njobs, nblocks, D, K, m);
+        case 1: return launch_db<5, 8>(c, jobs, njobs, nblocks, D, K, m);
+        case 2: return launch_db<6, 8>(c, jobs, njobs, nblocks, D, K, m);
+        case 3: return launch_db<8, 8>(c, jobs, njobs, nblocks, D, K, m);
+        case 4: return launch_db<12, 8>(c, jobs, njobs, nblocks, D, K, m);
+        case 5: return launch_db<16, 8>(c, jobs, njobs, nblocks, D, K, m);
+        default: return launch_db<8, 32>(c, jobs, njobs, nblocks, D, K, m);
     }
 }
 
-int swgb::db_warps_per_block(int K, int m) { return db_shape(K, m) == 2 ? 32 : 8; }
-
-int swgb::db_rows_per_pass(int K, int m) { return 32 * (db_shape(K, m) == 1 ? 16 : 8); }
-
 int swgb::db_launch(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m) {
-    switch (db_shape(K, m)) {
-        case 2: return launch_db<8, 32>(c, jobs, njobs, nblocks, D, K, m);
-        case 1: return launch_db<16, 8>(c, jobs, njobs, nblocks, D, K, m);
-        default: return launch_db<8, 8>(c, jobs, njobs, nblocks, D, K, m);
-    }
+    return db_launch_shape(c, db_shape(K, m), jobs, njobs, nblocks, D, K, m);
 }
 
 int swgb::db_view(const sw_db *db, DbView *v, int64_t *nseq, int32_t *max_code, int *device) {

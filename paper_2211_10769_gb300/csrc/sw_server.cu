@@ -76,10 +76,24 @@ size_t slot_bytes(const sw_server *S, int64_t m) {
     return (size_t)m + 256 + 2 * (size_t)std::max<int64_t>(1, S->nseq) * sizeof(int32_t) + 256;
 }
 
-// Retire a request that has seen every chunk: exact rescoring, top-k, free.
+// Retire a request that has seen every chunk: exact rescoring, top-k; its
+// slot (and the slot's device buffers, kept for the next request, since the
+// database size fixes them) becomes free.
+int retire_work(sw_server *S, Slot &s, Done &d);
+
 int retire(sw_server *S, Slot &s) {
-    sw_ctx *c = S->c;
     Done d;
+    const int rc = retire_work(S, s, d);
+    if (rc != SW_OK) d = Done{rc, {}};        // the request fails, the slot is freed all the same
+    S->done[s.ticket] = std::move(d);
+    S->cells_done += (long long)s.m * S->total_res;
+    S->mem_used -= slot_bytes(S, s.m);
+    s.active = false;
+    return rc;
+}
+
+int retire_work(sw_server *S, Slot &s, Done &d) {
+    sw_ctx *c = S->c;
     int32_t nflag = 0;
     CU(cudaMemcpyAsync(c->stage3.p, s.ctr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -100,11 +114,6 @@ int retire(sw_server *S, Slot &s) {
         const int2 *h = static_cast<const int2 *>(c->stage3.p);
         for (int i = 0; i < kk; ++i) d.hits.push_back(sw_dbhit{(int64_t)h[i].x, h[i].y, 0});
     }
-    S->done[s.ticket] = std::move(d);
-    S->cells_done += (long long)s.m * S->total_res;
-    S->mem_used -= slot_bytes(S, s.m);
-    s.active = false;
-    s.q.release(); s.scores.release(); s.ovf.release(); s.ctr.release();
     return SW_OK;
 }
 
@@ -180,36 +189,46 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     // chunk c = pairs c, c + C, c + 2C, ...: every chunk mixes long and short subjects
     const int np = S->view.npairs;
     const int p0 = S->cur_chunk, p1 = np, stride = S->chunks;
-    int64_t maxm = 0, summ = 0;
-    for (Slot *s : act) { maxm = std::max(maxm, s->m); summ += s->m; }
-    int resident = 0;
-    RC(db_resident_blocks(c, S->ds.K, (int)maxm, &resident));
-    const int W = db_warps_per_block(S->ds.K, (int)maxm);
-    const int rows = db_rows_per_pass(S->ds.K, (int)maxm);
     const int chunk_pairs = p0 < np ? (np - p0 + stride - 1) / stride : 0;
-    // a request's work is its query padded to whole passes of `rows` rows
-    auto padded = [&](int64_t m) { return (double)((m + rows - 1) / rows) * rows; };
-    double sumpad = 0;
-    for (Slot *s : act) sumpad += padded(s->m);
+    // the requests of a step run in groups of one tile shape each, every query with the shape
+    // that pads it least (one shape for all would pad a 100-residue query to a 512-row pass
+    // next to a long one); one launch per group
+    std::map<int, std::vector<Slot *>> groups;
+    for (Slot *s : act) groups[db_shape(S->ds.K, (int)s->m)].push_back(s);
     std::vector<DbJob> jobs;
-    int nblocks = 0;
-    for (Slot *s : act) {
-        DbJob j;
-        j.q = static_cast<const uint8_t *>(s->q.p);
-        j.m = (int32_t)s->m;
-        j.scoring = 0;
-        j.pair0 = p0; j.pair1 = p1; j.pair_stride = stride;
-        // blocks in proportion to the request's share of the step's work, kOversub times what
-        // fits at once: blocks of short jobs finish early and free their SMs for the others
-        const int share = (int)std::ceil(kOversub * resident * padded(s->m) / std::max(1.0, sumpad));
-        const int nb = std::max(1, std::min(share, (chunk_pairs + W - 1) / W));
-        j.block0 = nblocks;
-        nblocks += nb;
-        j.scores = static_cast<int32_t *>(s->scores.p);
-        j.ovf = static_cast<int32_t *>(s->ovf.p);
-        j.novf = static_cast<int32_t *>(s->ctr.p);
-        j.next_pair = static_cast<int32_t *>(s->ctr.p) + 1;
-        jobs.push_back(j);
+    struct Launch { int shape, job0, njobs, nblocks, maxm; };
+    std::vector<Launch> launches;
+    for (const auto &g : groups) {
+        const int shape = g.first;
+        int64_t maxm = 0;
+        for (Slot *s : g.second) maxm = std::max(maxm, s->m);
+        int resident = 0;
+        RC(db_resident_blocks_shape(c, shape, S->ds.K, (int)maxm, &resident));
+        const int W = db_shape_warps(shape), rows = db_shape_rows(shape);
+        // a request's work is its query padded to whole passes of `rows` rows
+        auto padded = [&](int64_t m) { return (double)((m + rows - 1) / rows) * rows; };
+        double sumpad = 0;
+        for (Slot *s : g.second) sumpad += padded(s->m);
+        Launch L{shape, (int)jobs.size(), (int)g.second.size(), 0, (int)maxm};
+        for (Slot *s : g.second) {
+            DbJob j;
+            j.q = static_cast<const uint8_t *>(s->q.p);
+            j.m = (int32_t)s->m;
+            j.scoring = 0;
+            j.pair0 = p0; j.pair1 = p1; j.pair_stride = stride;
+            // blocks in proportion to the request's share of the group's work, kOversub times what
+            // fits at once: blocks of short jobs finish early and free their SMs for the others
+            const int share = (int)std::ceil(kOversub * resident * padded(s->m) / std::max(1.0, sumpad));
+            const int nb = std::max(1, std::min(share, (chunk_pairs + W - 1) / W));
+            j.block0 = L.nblocks;
+            L.nblocks += nb;
+            j.scores = static_cast<int32_t *>(s->scores.p);
+            j.ovf = static_cast<int32_t *>(s->ovf.p);
+            j.novf = static_cast<int32_t *>(s->ctr.p);
+            j.next_pair = static_cast<int32_t *>(s->ctr.p) + 1;
+            jobs.push_back(j);
+        }
+        launches.push_back(L);
     }
     const size_t jb = jobs.size() * sizeof(DbJob);
     RC(S->jobs.ensure(jb));
@@ -222,7 +241,9 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     if (chunk_pairs > 0) {
         DbView v = S->view;
         v.maxlen = std::max(1, db_chunk_maxlen(S->db, p0, p0 + 1));     // pairs are sorted longest first
-        RC(db_launch(c, static_cast<const DbJob *>(S->jobs.p), (int)jobs.size(), nblocks, v, S->ds.K, (int)maxm));
+        for (const Launch &L : launches)
+            RC(db_launch_shape(c, L.shape, static_cast<const DbJob *>(S->jobs.p) + L.job0, L.njobs, L.nblocks, v,
+                               S->ds.K, L.maxm));
     }
     CU(cudaMemcpyAsync(c->stage3.p, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -230,10 +251,14 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     std::memcpy(&e, c->stage3.p, sizeof(int));
     RC(map_kernel_error(e));
     S->cur_chunk = (S->cur_chunk + 1) % S->chunks;
+    int first = SW_OK;                       // every finished request retires, even after a failure
     for (Slot *s : act) {
-        if (++s->visited >= S->chunks) RC(retire(S, *s));
+        if (++s->visited >= S->chunks) {
+            const int rc = retire(S, *s);
+            if (rc != SW_OK && first == SW_OK) first = rc;
+        }
     }
-    return SW_OK;
+    return first;
 }
 
 extern "C" int sw_server_poll(sw_server *S, uint64_t ticket, sw_dbhit *hits, int32_t *nhits) {

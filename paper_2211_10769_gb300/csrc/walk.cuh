@@ -182,6 +182,19 @@ __device__ __forceinline__ int window_nibble(const WalkWindow &m, const Word *wi
     return (int)((unsigned long long)w >> (4 * (rr - g * R))) & 15;
 }
 
+// The walk's start taken from the end cell reduced on the device (res: score,
+// row, column), for an alignment done in one round without a round trip to
+// the host: the end cell in state H, or nothing to walk (done = 3, parked at
+// cell (1, 1), a cell every window can hold) when the local score is 0 or the
+// end cell lies on the border.
+static __global__ void walk_start_kernel(const int4 *res, int local, WalkState *st) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int4 r = *res;
+    WalkState w{r.y, r.z, 0, 0, 0, -1, 0};
+    if ((local && r.x <= 0) || r.y <= 0 || r.z <= 0) { w.i = 1; w.j = 1; w.done = 3; }
+    *st = w;
+}
+
 template <typename Word, int R>
 __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const TileTable<Word> T, WalkState *st, int2 *runs,
                                                           long long max_iters)

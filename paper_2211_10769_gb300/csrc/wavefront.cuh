@@ -206,7 +206,10 @@ struct LaneState {
     int ub, fb, udiag0;
     int bk, bj;
     int rlast;        // the other algorithms: the lane's row holding the task's last row, or -1
-    int track;        // ... and whether that row is an end row at every column (semi-global, overlap)
+    unsigned track;   // ... as a bit mask (1 << rlast) where that row is an end row at every column
+                      // (semi-global, overlap), else 0.  A mask, not a comparison with rlast: a
+                      // chain of selects on r == rlast is turned into an indexed load of U by the
+                      // compiler, which moves the lane state to local memory.
 };
 
 // The lane's end cell is the first of its cells in row-major order holding
@@ -286,7 +289,7 @@ __device__ __forceinline__ void lane_step(LaneState<R> &st, const uint32_t (&pw)
         // semi-global and overlap: the task's last row is an end row at every column
         int ck = st.bk;
 #pragma unroll
-        for (int r = 0; r < R; ++r) ck = (st.track && r == st.rlast) ? row_key<R>(st.U[r], r) : ck;
+        for (int r = 0; r < R; ++r) ck = ((st.track >> r) & 1u) ? row_key<R>(st.U[r], r) : ck;
         st.bj = ck > st.bk ? j : st.bj;
         st.bk = max(st.bk, ck);
     } else {
@@ -599,7 +602,7 @@ wavefront_kernel(const FillLaunch L)
                     st.U[r] = (int)left_border_h(SC.alg, (long long)T.row0 + grow + r + 1, go, ge) - go;
                 st.udiag0 = (int)left_border_h(SC.alg, (long long)T.row0 + grow, go, ge) - go;
                 st.rlast = (T.rows - 1 >= grow && T.rows - 1 < grow + R) ? T.rows - 1 - grow : -1;
-                st.track = SC.alg == kAlgSemiGlobal || SC.alg == kAlgOverlap;
+                st.track = ((SC.alg == kAlgSemiGlobal || SC.alg == kAlgOverlap) && st.rlast >= 0) ? 1u << st.rlast : 0u;
             }
             st.ub = st.U[R - 1];
             st.fb = kNeg;
@@ -761,13 +764,14 @@ wavefront_kernel(const FillLaunch L)
                     // the best of the task's last row (semi-global, overlap), then the last
                     // column: every row for the overlap algorithm, the last row for the global one
                     cs = kNoScore; cj = 0x7fffffff; ci = 0x7fffffff;
-                    if (st.track && st.rlast >= 0 && st.bj >= 0) {
+                    if (st.track && st.bj >= 0) {
                         cs = (st.bk >> 4) + go; cj = st.bj + 1; ci = T.row0 + grow + st.rlast + 1;
                     }
+                    const unsigned lastbit = st.rlast >= 0 ? 1u << st.rlast : 0u;
                     if (n > 0 && (SC.alg == kAlgOverlap || SC.alg == kAlgGlobal)) {
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            const bool end = SC.alg == kAlgOverlap ? grow + r < T.rows : r == st.rlast;
+                            const bool end = SC.alg == kAlgOverlap ? grow + r < T.rows : ((lastbit >> r) & 1u);
                             const int sc = st.U[r] + go, ii = T.row0 + grow + r + 1;
                             if (end && cand_better(sc, n, ii, cs, cj, ci)) { cs = sc; cj = n; ci = ii; }
                         }

@@ -49,6 +49,20 @@ def test_small_database_all_scores(ctx, oracle_mod):
         assert {s for s, _ in top} & set(pdb.planted[qi])     # the planted homologs are found
 
 
+def test_every_tile_shape(ctx, oracle_mod):
+    """Query lengths that pick each tile shape of the packed search (4, 5, 6,
+    8, 12 and 16 rows a lane, and 32-warp blocks for long queries), with one
+    or several passes and the last pass partly padding."""
+    sc = W.protein_scoring()
+    lengths = (1, 31, 100, 128, 144, 160, 161, 190, 250, 300, 350, 384, 464, 700, 1000, 1500, 4100)
+    qs = W.protein_queries(lengths, seed_offset=760)
+    pdb = W.protein_db(400, queries=qs, seed_offset=770)
+    subjects = [pdb.subject(s) for s in range(pdb.nseq)]
+    db = _db(ctx, subjects)
+    for q in qs:
+        _check_all(ctx, oracle_mod, db, subjects, q, sc)
+
+
 def test_long_query_and_dna(ctx, oracle_mod):
     sc = W.protein_scoring()
     q = W.protein_queries((5478,))[0]

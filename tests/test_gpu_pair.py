@@ -17,21 +17,26 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-@pytest.fixture(scope="module", params=["packed16", "int32"])
+@pytest.fixture(scope="module", params=["packed16", "int32", "one_round"])
 def ctx(request):
     """A context on the packed 16-bit pair fill (the default where it is
-    exact) and one restricted to the int32 fill: every test runs on both."""
+    exact), one restricted to the int32 fill, and one that reconstructs
+    small pairs in one round (whole-matrix traceback bits) instead of through
+    checkpoints and bands of traceback tiles: every test runs on all three."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
-    old = os.environ.get("SWGB_P16")
-    os.environ["SWGB_P16"] = "1" if request.param == "packed16" else "0"
+    env = {"SWGB_P16": "0" if request.param == "int32" else "1",
+           "SWGB_ONE_ROUND": "1" if request.param == "one_round" else "0"}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         c = binding.Context(0)
     finally:
-        if old is None:
-            del os.environ["SWGB_P16"]
-        else:
-            os.environ["SWGB_P16"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
     yield c
     c.close()
 
@@ -310,6 +315,21 @@ def test_strip_heights(oracle_mod, monkeypatch, fwd):
             assert (h.score, h.a_end, h.b_end) == (want.score, want.a_end, want.b_end), fwd
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("side", [8192, 8193])
+def test_align_one_round_limit(ctx, oracle_mod, side):
+    """The largest pair reconstructed in one round (both sides 8,192, one
+    traceback tile of 8,192 x 8,192 cells) and the smallest that is not."""
+    seed = W.BASE_SEED + 9900 + side
+    A = W.uniform_dna(side, seed)
+    B = W.mutate(A, 4, seed + 1, p_sub=0.1, p_indel=0.02)
+    B = np.concatenate([B, W.uniform_dna(side, seed + 2)])[:side]
+    S = W.dna_matrix()
+    want = oracle_mod.sw_align_ptr(A, B, S, 5, 2)
+    got = ctx.align(A, B, S, 5, 2)
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end, got.cigar) == \
+        (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end, want.cigar)
 
 
 def test_kernel_timing(ctx):

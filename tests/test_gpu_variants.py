@@ -14,11 +14,21 @@ pytestmark = pytest.mark.gpu
 ALGS = (1, 2, 3)
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["banded", "one_round"])
+def ctx(request):
+    """Small pairs reconstructed through checkpoints and bands of traceback
+    tiles (the default) and in one round."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
-    c = binding.Context(0)
+    old = os.environ.get("SWGB_ONE_ROUND")
+    os.environ["SWGB_ONE_ROUND"] = "1" if request.param == "one_round" else "0"
+    try:
+        c = binding.Context(0)
+    finally:
+        if old is None:
+            del os.environ["SWGB_ONE_ROUND"]
+        else:
+            os.environ["SWGB_ONE_ROUND"] = old
     yield c
     c.close()
 
@@ -122,6 +132,31 @@ def test_score_long_pair(ctx, oracle_mod, alg):
     sc = W.dna_scoring()
     A, B = W.dna_long_pair(20_000)
     _score_case(ctx, oracle_mod, A, B, sc.matrix, sc.gap_open, sc.gap_extend, alg)
+
+
+@pytest.mark.parametrize("R", [12, 16])
+@pytest.mark.parametrize("alg", ALGS)
+def test_strip_heights(oracle_mod, monkeypatch, alg, R):
+    """The taller strips that long pairs take (12 and 16 rows a lane, forced
+    here): score and alignment across several strips, with the task's last row
+    inside a lane, equal the oracle's."""
+    from paper_2211_10769_gb300 import binding
+    monkeypatch.setenv("SWGB_FWD", "%d,4" % R)
+    c = binding.Context(0)
+    try:
+        seed = W.BASE_SEED + 15700 + 10 * R + alg
+        sc = W.dna_scoring()
+        A = W.uniform_dna(3 * 4 * 32 * R + 37, seed)
+        B = W.mutate(A, 4, seed + 1, p_sub=0.1, p_indel=0.02)
+        _score_case(c, oracle_mod, A, B, sc.matrix, sc.gap_open, sc.gap_extend, alg)
+        _align_case(c, oracle_mod, A, B, sc.matrix, sc.gap_open, sc.gap_extend, alg)
+        p = W.protein_scoring()
+        P = W.random_protein(2 * 4 * 32 * R + 5, seed + 2)
+        Q = W.mutate(P, 20, seed + 3, p_sub=0.3)
+        _score_case(c, oracle_mod, P, Q, p.matrix, p.gap_open, p.gap_extend, alg)
+        _align_case(c, oracle_mod, P[: 4 * 32 * R + 9], Q, p.matrix, p.gap_open, p.gap_extend, alg)
+    finally:
+        c.close()
 
 
 def test_batch_mixed_algorithms(ctx, oracle_mod):
