@@ -185,19 +185,17 @@ struct P16Lane {
 // left of the task hold the border state (H = 0), which is never a best.
 template <int R, int PK, int QS, bool TAIL>
 __device__ __forceinline__ void p16_step(P16Lane<R> &st, const uint32_t (&pw)[R / 2], const uint32_t (&pwp)[R / 2],
-                                         int2 top, int s, int lane, int n, unsigned nge2, unsigned ngo2,
+                                         uint2 top, int s, int lane, int n, unsigned nge2, unsigned ngo2,
                                          unsigned neg2, int2 *rout)
 {
     constexpr int H = R / 2;
     const int j = s - 2 * lane;
     const unsigned su = __shfl_up_sync(kFull, st.ub, 1);
     const unsigned sf = __shfl_up_sync(kFull, st.fb, 1);
-    // lane 0: the row above is the strip's boundary row (scaled, absolute: H - open and F),
-    // taken to its base; its F of the first row is max(F - extend, H - open)
-    const int tu = __viaddmax_s32(top.x, -st.B, kNeg16p);
-    const int tf = __viaddmax_s32(__viaddmax_s32(top.y, p16_lo(nge2), top.x), -st.B, kNeg16p);
-    const unsigned srcu = lane == 0 ? ((unsigned)tu << 16) : su;
-    const unsigned srcf = lane == 0 ? ((unsigned)tf << 16) : sf;
+    // lane 0: the row above is the strip's boundary row, already in lane 0's base and in the
+    // high halves (p16_top_row)
+    const unsigned srcu = lane == 0 ? top.x : su;
+    const unsigned srcf = lane == 0 ? top.y : sf;
     // low half: the row above the top half at j (the high half of the source, moved from
     // lane t-1's base to this one); high half: this lane's top half's last row at j - 1.
     // fb carries F of the row below a half's last row, so f is already the first row's F.
@@ -239,6 +237,15 @@ __device__ __forceinline__ void p16_step(P16Lane<R> &st, const uint32_t (&pw)[R 
     st.bcol[1] = ph ? st.bcol[1] : j - 1;
 }
 
+// Lane 0's row above at one step, from the strip's boundary row v (scaled,
+// absolute: H - open and F): both taken to lane 0's base B0 and into the high
+// halves, the F as the first row's F, max(F - extend, H - open).
+__device__ __forceinline__ uint2 p16_top_row(int2 v, int B0, int ge8) {
+    const int tu = __viaddmax_s32(v.x, -B0, kNeg16p);
+    const int tf = __viaddmax_s32(__viaddmax_s32(v.y, -ge8, v.x), -B0, kNeg16p);
+    return make_uint2((unsigned)tu << 16, (unsigned)tf << 16);
+}
+
 #ifndef SWGB_P16_UNROLL
 constexpr int fill16_unroll(int R) { return R <= 8 ? 8 : 16; }   // measured on GB300 (2, 4, 8, 16)
 #else
@@ -269,6 +276,8 @@ wavefront16_kernel(const FillLaunch L)
     __shared__ int s_task;
     __shared__ volatile int s_abort;
     __shared__ int4 s_cand[W];
+    __shared__ uint2 s_top[W][CH];                   // lane 0's rows above for one chunk (p16_top_row)
+    static_assert(CH <= 32 && (CH & (CH - 1)) == 0, "one boundary entry a lane, a power of two");
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -365,7 +374,7 @@ wavefront16_kernel(const FillLaunch L)
             uint32_t pw[R / 2], pwp[R / 2];
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);
-            int2 top;
+            uint2 top;
             // the head of a long strip chain (warp 0 of strip 0) runs a little slower than it
             // could (L.pace_permille of its chunk time), so that every warp after it has slack
             // and catches up after a slow chunk instead of keeping the delay: without it each
@@ -387,7 +396,6 @@ wavefront16_kernel(const FillLaunch L)
                     if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (c * (K + 1) + cprev) * pstride, pw);
                     else p16_load<R, PK, NL>(prow + c * pstride, pw);
                     cprev = c;
-                    top = rin[s0 & (QS - 1)];
                     loaded = true;
                 }
                 {   // new lane base from the top half's first row at its last column; the best
@@ -412,6 +420,19 @@ wavefront16_kernel(const FillLaunch L)
                     st.din2 = lane == 0 ? 0u : p16_pack(bup - Bn, 0);
                     st.kbest = p16_pack(min(st.best[0] - Bn, 32767), min(st.best[1] - Bn, 32767));
                 }
+                {   // lane 0's rows above for the chunk's steps, taken to its new base once per
+                    // chunk (one entry a lane) rather than once per step; entries at or past n
+                    // read as -infinity.  The wait above made entries below s0 + CH + 1 ready.
+                    const int B0 = __shfl_sync(kFull, st.B, 0);
+                    __syncwarp();
+                    if (lane < CH) {
+                        const int sk = s0 + lane;
+                        const int2 v = sk < n ? rin[sk & (QS - 1)] : make_int2(kNeg, kNeg);
+                        s_top[warp][lane] = p16_top_row(v, B0, -p16_lo(nge2));
+                    }
+                    __syncwarp();
+                    top = s_top[warp][0];
+                }
                 if (s0 + CH + 1 <= n) {
                     // steady state: lane 0's prefetched column stays inside the task; columns
                     // left of the task (first chunks) compute the border state on padding
@@ -419,7 +440,7 @@ wavefront16_kernel(const FillLaunch L)
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
                         const int cn = min((int)bring[(s + 1 - 2 * lane) & (QB - 1)], K);
-                        const int2 topn = rin[(s + 1) & (QS - 1)];
+                        const uint2 topn = s_top[warp][(k + 1) & (CH - 1)];   // (unused after the last step)
                         uint32_t pwn[R / 2];
                         if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (cn * (K + 1) + cprev) * pstride, pwn);
                         else p16_load<R, PK, NL>(prow + cn * pstride, pwn);
@@ -441,7 +462,7 @@ wavefront16_kernel(const FillLaunch L)
                             const int s = s0 + gs + k;
                             const int jn = s + 1 - 2 * lane;
                             const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
-                            const int2 topn = s + 1 < n ? rin[(s + 1) & (QS - 1)] : make_int2(kNeg, kNeg);
+                            const uint2 topn = s_top[warp][(gs + k + 1) & (CH - 1)];
                             uint32_t pwn[R / 2];
                             if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (cn * (K + 1) + cprev) * pstride, pwn);
                             else p16_load<R, PK, NL>(prow + cn * pstride, pwn);
