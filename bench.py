@@ -60,8 +60,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed CPU oracle sample")
     ap.add_argument("--workloads", default="all",
                     help="comma list of the other workloads to measure after the headline: "
-                         "dna2k,variants,dbsearch,batch,serve,dna5m (default all; 'none' for the headline only)")
+                         "dna2k,variants,dbsearch,batch,serve,dna5m,bounded (default all; 'none' for the headline only)")
     ap.add_argument("--serve-requests", type=int, default=500, help="requests per arrival rate")
+    ap.add_argument("--bounded-length", type=int, default=5_000_000,
+                    help="length of the long pair aligned under a small checkpoint budget")
+    ap.add_argument("--bounded-budget-mb", type=int, default=1024, help="that checkpoint budget (MB)")
     ap.add_argument("--serve-rates", default="10,20,50,2000",
                     help="arrival rates (requests/s): below, near and above the device's capacity")
     return ap.parse_args()
@@ -411,7 +414,7 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_leg(args)
         wl = [] if args.workloads == "none" else (
-            ["dna2k", "variants", "dbsearch", "batch", "serve", "dna5m"] if args.workloads == "all"
+            ["dna2k", "variants", "dbsearch", "batch", "serve", "dna5m", "bounded"] if args.workloads == "all"
             else args.workloads.split(","))
         if wl and args.mode == "align":
             from paper_2211_10769_gb300 import bench_workloads as BW

@@ -18,6 +18,7 @@ CUDA events on the context's stream and returns a small dict:
 """
 from __future__ import annotations
 
+import hashlib
 import statistics
 import time
 
@@ -248,7 +249,47 @@ def dna5m(ctx, torch, stream, args):
             "seconds": round(t, 3), "gcups": round(cells / t / 1e9, 1),
             "kernel_s": {nm: round(v[0] / 1e3, 3) for nm, v in k.items()},
             "result": {"score": ref.score, "a": [ref.a_begin, ref.a_end], "b": [ref.b_begin, ref.b_end],
-                       "cigar_len": len(ref.cigar)}}
+                       "cigar_len": len(ref.cigar), "cigar_sha256": hashlib.sha256(ref.cigar.encode()).hexdigest()}}
+
+
+def bounded(ctx, torch, stream, args):
+    """sw_align of the long pair (default 5 Mbp) under a small checkpoint budget (two checkpoint
+    levels): one timed call in a context of its own, and the device memory that context holds."""
+    import os
+    from .binding import Context, KT_FILL, KT_FILL_TB, KT_WALK
+    sc = W.dna_scoring()
+    A, B = W.dna_long_pair(args.bounded_length)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    old = os.environ.get("SWGB_CKPT_BUDGET_MB")
+    os.environ["SWGB_CKPT_BUDGET_MB"] = str(args.bounded_budget_mb)
+    try:
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        bctx = Context(0, stream)
+    finally:
+        if old is None:
+            del os.environ["SWGB_CKPT_BUDGET_MB"]
+        else:
+            os.environ["SWGB_CKPT_BUDGET_MB"] = old
+    try:
+        bctx.timing(True)
+        ts = _timed(torch, stream, lambda: bctx.align(dA, dB, sc.matrix, sc.gap_open, sc.gap_extend), 1)
+        k = {nm: bctx.kernel_time(kind) for nm, kind in (("fill", KT_FILL), ("fill_tb", KT_FILL_TB),
+                                                        ("walk", KT_WALK))}
+        aln = bctx.align(dA, dB, sc.matrix, sc.gap_open, sc.gap_extend)
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        bctx.close()
+    t = ts[0]
+    cells = len(A) * len(B)
+    return {"workload": "dna_pair_long_align_bounded_memory", "m": len(A), "n": len(B), "cells": cells,
+            "checkpoint_budget_mb": args.bounded_budget_mb,
+            "context_device_mb": round((free0 - free1) / 2**20, 1),
+            "seconds": round(t, 3), "gcups": round(cells / t / 1e9, 1),
+            "kernel_s": {nm: round(v[0] / 1e3, 3) for nm, v in k.items()},
+            "note": "fill counts the forward fill and the coarse tiles' refills",
+            "result": {"score": aln.score, "a": [aln.a_begin, aln.a_end], "b": [aln.b_begin, aln.b_end],
+                       "cigar_len": len(aln.cigar), "cigar_sha256": hashlib.sha256(aln.cigar.encode()).hexdigest()}}
 
 
 def run_all(names, args):
@@ -259,7 +300,7 @@ def run_all(names, args):
     res = {}
     for nm in names:
         fn = {"dna2k": dna2k, "variants": variants, "dbsearch": dbsearch, "batch": batch, "serve": serve,
-              "dna5m": dna5m}[nm]
+              "dna5m": dna5m, "bounded": bounded}[nm]
         t0 = time.perf_counter()
         try:
             res[nm] = fn(ctx, torch, stream, args)

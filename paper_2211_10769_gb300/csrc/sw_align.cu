@@ -138,6 +138,64 @@ int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int
     }
 }
 
+// One checkpoint level while its tile side stays within this; two levels above it.
+constexpr long long kMaxOneLevelBT = 16384;
+
+// Two levels of checkpoints: fill the part of coarse tile (CI, CJ) above and left
+// of (Wi0, Wj0) again, entered from the forward fill's checkpoint row above it and
+// its staircase column left of it, keeping checkpoint rows and staircase columns
+// every BT2 inside it: the int32 fill with the forward fill's rows per lane (so
+// that it can enter that fill's staircase column, in either form).  Memory for
+// the refill's checkpoints is about 16 BT1^2 / BT2 bytes, for any pair size.
+int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t n, const DevScoring &ds,
+                       const FillConfig &fwd, bool fold, int aux_rows, const int2 *rowck, const int2 *colck,
+                       const int2 *colaux, long long colck_ld, long long colaux_ld, long long CI, long long CJ,
+                       long long R0c, long long C0c, long long Wi0, long long Wj0, long long BT2,
+                       const int2 **rowck2, const int2 **colck2, const int2 **colaux2, long long *ld2, long long *N2) {
+    FillConfig fc{fwd.R, 4};
+    fc.alg = fwd.alg;
+    const int HC2 = 4 * 32 * fc.R;
+    const long long M2 = Wi0 - R0c, W2 = Wj0 - C0c;
+    FillTask t{};
+    t.a = da + R0c; t.b = db + C0c;
+    t.rows = (int32_t)M2; t.ncols = (int32_t)W2;
+    t.strip_warps = 4;
+    t.nstrips = (int32_t)((M2 + HC2 - 1) / HC2);
+    t.nslot = std::min(t.nstrips, 4);
+    RC(c->bnd.ensure((size_t)t.nslot * (size_t)W2 * sizeof(int2)));
+    t.bnd = static_cast<int2 *>(c->bnd.p);
+    t.top = CI > 0 ? rowck + (size_t)(CI - 1) * n + C0c : nullptr;
+    if (CJ > 0) {
+        t.left = colck + (size_t)(CJ - 1) * colck_ld + R0c;
+        t.left_aux = colaux + (size_t)(CJ - 1) * colaux_ld + R0c / aux_rows;
+        t.left_split = fwd.P16 ? 1 : 0;
+    }
+    t.row0 = (int32_t)R0c;
+    t.col0 = (int32_t)C0c;
+    const long long nr = std::max<long long>(1, M2 / BT2), nc = std::max<long long>(1, W2 / BT2);
+    t.ckpt_every = (int32_t)(BT2 / HC2);
+    RC(c->ckpt2.ensure((size_t)nr * (size_t)W2 * sizeof(int2)));
+    t.ckpt = static_cast<int2 *>(c->ckpt2.p);
+    t.colck_every = (int32_t)BT2;
+    t.colck_ld = (long long)t.nstrips * HC2;
+    RC(c->colck2.ensure((size_t)nc * (size_t)t.colck_ld * sizeof(int2)));
+    RC(c->colaux2.ensure((size_t)nc * (size_t)(t.colck_ld / fc.R) * sizeof(int2)));
+    // the fill writes column checkpoints at colck + k ld + (row0 + row) and their row-group
+    // records at colck_aux + k ld / R + (row0 + row) / R: based so that row0 lands on 0
+    t.colck = static_cast<int2 *>(c->colck2.p) - R0c;
+    t.colck_aux = static_cast<int2 *>(c->colaux2.p) - R0c / fc.R;
+    RC(run_fill(c, fc, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
+    int e = 0;
+    RC(read_err(c, &e));          // synchronises: the next fill reuses the staging buffer
+    RC(map_kernel_error(e));
+    *rowck2 = static_cast<const int2 *>(c->ckpt2.p);
+    *colck2 = static_cast<const int2 *>(c->colck2.p);
+    *colaux2 = static_cast<const int2 *>(c->colaux2.p);
+    *ld2 = t.colck_ld;
+    *N2 = W2;
+    return SW_OK;
+}
+
 // Sides up to this many cells take the one-round reconstruction below.
 constexpr int64_t kOneRoundSide = 8192;
 
@@ -303,15 +361,41 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     // one auxiliary record per half-group of R/2 rows
     const int aux_rows = fwd.P16 ? fwd.R / 2 : fwd.R;
     const int HT = fill_rows_per_strip(tbc);
+    const int HC2 = 4 * 32 * fwd.R;                // strip height of a coarse tile's refill (int32, 4 warps)
     const long long BL = std::lcm((long long)HC, (long long)HT);
-    long long BT = BL * ((1024 + BL - 1) / BL);
+    const long long BL2 = std::lcm((long long)HC2, (long long)HT);
     auto ck_bytes = [&](long long bt) {
         return (size_t)((m / bt) * n + (n / bt) * m) * sizeof(int2);
     };
-    while (ck_bytes(BT) > c->ckpt_budget && BT < (1LL << 30)) BT *= 2;
-    // checkpoint columns are stored at chunk ends: BT must be a multiple of the chunk
-    if (BT % HC != 0 || BT % HT != 0 || BT % kCH != 0 || BT > (1LL << 30)) return SW_EINVAL;
-    const long long nrowck = std::max<long long>(1, m / BT), ncolck = std::max<long long>(1, n / BT);
+    // BT1: the forward fill's checkpoint spacing; BT2: the traceback tiles' side.  One level
+    // (BT1 = BT2) while the checkpoints fit the budget at a tile side up to kMaxOneLevelBT;
+    // else two: coarse checkpoints every BT1 (half the budget), and each coarse tile the
+    // path enters is filled again from them with fine checkpoints every BT2 (the other half)
+    long long BT1 = BL * ((1024 + BL - 1) / BL);
+    while (ck_bytes(BT1) > c->ckpt_budget && BT1 < (1LL << 30)) BT1 *= 2;
+    long long BT2 = BT1;
+    if (c->two_level_bt1 > 0) {                     // SWGB_TWO_LEVEL: the sides, checked below
+        BT1 = c->two_level_bt1;
+        BT2 = c->two_level_bt2;
+    } else if (BT1 > kMaxOneLevelBT) {
+        // level-1 checkpoints ~ 16 m n / BT1 bytes, a refill's ~ 16 BT1^2 / BT2: each within half
+        // the budget, BT2 doubled until the second fits
+        for (BT2 = BL2 * ((1024 + BL2 - 1) / BL2);; BT2 *= 2) {
+            const long long step = std::lcm(BT2, BL);
+            BT1 = step * std::max<long long>(2, (4 * BT2 + step - 1) / step);
+            while (ck_bytes(BT1) > c->ckpt_budget / 2 && BT1 < (1LL << 30)) BT1 += step;
+            if ((double)2 * (double)(BT1 / BT2) * (double)BT1 * sizeof(int2) <= (double)(c->ckpt_budget / 2) ||
+                BT2 >= kMaxOneLevelBT)
+                break;
+        }
+    }
+    const bool two = BT2 != BT1;
+    // checkpoint columns are stored at chunk ends: the sides must be multiples of the chunk
+    if (BT1 % HC != 0 || BT2 % HT != 0 || BT1 % kCH != 0 || BT2 % kCH != 0 || BT1 % BT2 != 0 ||
+        (two && BT2 % HC2 != 0) || BT1 > (1LL << 30))
+        return SW_EINVAL;
+    const long long BT = BT2;
+    const long long nrowck = std::max<long long>(1, m / BT1), ncolck = std::max<long long>(1, n / BT1);
 
     // ---- 1. forward fill with row and column checkpoints
     FillTask t{};
@@ -323,10 +407,10 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     t.nslot = std::min(t.nstrips, 4);
     RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
     t.bnd = static_cast<int2 *>(c->bnd.p);
-    t.ckpt_every = (int32_t)(BT / HC);
+    t.ckpt_every = (int32_t)(BT1 / HC);
     RC(c->ckpt.ensure((size_t)nrowck * (size_t)n * sizeof(int2)));
     t.ckpt = static_cast<int2 *>(c->ckpt.p);
-    t.colck_every = (int32_t)BT;
+    t.colck_every = (int32_t)BT1;
     t.colck_ld = (long long)t.nstrips * HC;     // rows padded to whole strips (the padding is written)
     RC(c->colck.ensure((size_t)ncolck * (size_t)t.colck_ld * sizeof(int2)));
     RC(c->colaux.ensure((size_t)ncolck * (size_t)(t.colck_ld / aux_rows) * sizeof(int2)));
@@ -376,34 +460,60 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->tb.ensure(tile_bytes * maxtiles));
     RC(c->tbbnd.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
     RC(c->misc.ensure(table_cap * sizeof(void *)));
+    // level 1: the forward fill's checkpoints (every BT1); level 2 (two levels only): those of
+    // the current coarse tile's refill (every BT2 inside it), over rows [R0c, Wi0) and
+    // columns [C0c, Wj0), the part of the coarse tile above and left of where the walk entered
     const int2 *rowck = t.ckpt, *colck = t.colck, *colaux = t.colck_aux;
     const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / aux_rows;
+    long long CIc = -1, CJc = -1, R0c = 0, C0c = 0, Wi0 = m, Wj0 = n, ld2 = 0, N2 = 0;
+    const int2 *rowck2 = nullptr, *colck2 = nullptr, *colaux2 = nullptr;
     int prev_i = -1, prev_j = -1, prev_state = -1;
     while (true) {
+        if (two && ((w.i - 1) / BT1 != CIc || (w.j - 1) / BT1 != CJc)) {
+            CIc = (w.i - 1) / BT1;
+            CJc = (w.j - 1) / BT1;
+            R0c = CIc * BT1; C0c = CJc * BT1;
+            Wi0 = w.i; Wj0 = w.j;
+            RC(refill_coarse_tile(c, da, db, n, ds, fwd, fold, aux_rows, rowck, colck, colaux, colck_ld, colaux_ld,
+                                  CIc, CJc, R0c, C0c, Wi0, Wj0, BT2, &rowck2, &colck2, &colaux2, &ld2, &N2));
+        }
         const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
-        const int I0 = std::max(0, I - band + 1), J0 = std::max(0, J - band);
+        const int It0 = (int)(R0c / BT), Jt0 = (int)(C0c / BT);       // the region's first tile row, column
+        const int I0 = std::max(It0, I - band + 1), J0 = std::max(Jt0, J - band);
         const int nI = I - I0 + 1, nJ = J - J0 + 1;
         std::vector<const void *> table((size_t)nI * nJ, nullptr);
         std::vector<FillTask> tasks;
         long long tickets = 0;
-        for (int d = 0; d < band && I - d >= 0; ++d) {
+        for (int d = 0; d < band && I - d >= It0; ++d) {
             for (int dl = -1; dl <= 1; ++dl) {
                 const int ti = I - d, tj = J - d + dl;
-                if (tj < 0 || tj > J) continue;
+                if (tj < Jt0 || tj > J) continue;
                 FillTask u{};
                 const long long r0 = (long long)ti * BT, c0 = (long long)tj * BT;
                 u.a = da + r0;
                 u.b = db + c0;
-                u.rows = (int32_t)std::min<long long>(BT, m - r0);
-                u.ncols = (int32_t)std::min<long long>(BT, n - c0);
+                u.rows = (int32_t)std::min<long long>(BT, Wi0 - r0);
+                u.ncols = (int32_t)std::min<long long>(BT, Wj0 - c0);
                 u.strip_warps = tsw;
                 u.nstrips = (u.rows + HS - 1) / HS;
                 u.scoring = 0;
                 u.ticket0 = tickets;
-                u.top = ti > 0 ? rowck + (size_t)(ti - 1) * n + c0 : nullptr;
-                u.left = tj > 0 ? colck + (size_t)(tj - 1) * colck_ld + r0 : nullptr;
-                u.left_aux = tj > 0 ? colaux + (size_t)(tj - 1) * colaux_ld + r0 / aux_rows : nullptr;
-                u.left_split = fwd.P16 ? 1 : 0;
+                // the row above the tile and the column left of it: the matrix border, a
+                // forward-fill checkpoint (on a coarse boundary) or a refill checkpoint
+                if (r0 == 0) u.top = nullptr;
+                else if (r0 % BT1 == 0) u.top = rowck + (size_t)(r0 / BT1 - 1) * n + c0;
+                else u.top = rowck2 + (size_t)((r0 - R0c) / BT - 1) * N2 + (c0 - C0c);
+                if (c0 == 0) {
+                    u.left = nullptr; u.left_aux = nullptr;
+                } else if (c0 % BT1 == 0) {
+                    u.left = colck + (size_t)(c0 / BT1 - 1) * colck_ld + r0;
+                    u.left_aux = colaux + (size_t)(c0 / BT1 - 1) * colaux_ld + r0 / aux_rows;
+                    u.left_split = fwd.P16 ? 1 : 0;
+                } else {
+                    u.left = colck2 + (size_t)((c0 - C0c) / BT - 1) * ld2 + (r0 - R0c);
+                    u.left_aux = colaux2 + (size_t)((c0 - C0c) / BT - 1) * (ld2 / R) + (r0 - R0c) / R;
+                    u.left_split = 0;
+                }
                 const size_t k = tasks.size();
                 u.nslot = std::min(u.nstrips, 2);
                 u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;

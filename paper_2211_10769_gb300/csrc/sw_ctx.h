@@ -78,10 +78,13 @@ struct sw_ctx {
     int pace_permille = 0;            // slow-down of a strip chain's first warp (FillLaunch; off: measured no gain)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
     bool one_round = false;           // sw_align of small pairs in one round (whole-matrix traceback bits)
+    long long two_level_bt1 = 0;      // sw_align: forced coarse / fine checkpoint sides (0 = by budget)
+    long long two_level_bt2 = 0;
     int tb_strip_warps = 0;           // compute warps per traceback strip (0 = all)
     size_t ckpt_budget = 0;           // bytes of checkpoint rows kept by sw_align
     size_t tb_budget = 0;             // bytes of traceback bits per row group
     swgb::DevBuf seq_a, seq_b, tasks, scorings, ticket, prog, cand, result, err, bnd, ckpt, colck, colaux, tb,
+        ckpt2, colck2, colaux2,
         tbbnd, runs, walk, misc, dbscratch, dbslots, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
     std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class

@@ -44,18 +44,27 @@ def _piece_score(A, B, S, go, ge, i, j, runs):
     return sc, i, j
 
 
-def test_dna_5mbp_pair(oracle_mod):
+@pytest.fixture(scope="module")
+def long5m():
+    """The 5 Mbp pair, its alignment and its score-mode hit with the default
+    checkpoint budget (one checkpoint level)."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
     sc = W.dna_scoring()
-    S, go, ge = sc.matrix, sc.gap_open, sc.gap_extend
     A, B = W.dna_long_pair(5_000_000)
     ctx = binding.Context(0)
     try:
-        aln = ctx.align(A, B, S, go, ge)
-        hit = ctx.score(A, B, S, go, ge)
+        aln = ctx.align(A, B, sc.matrix, sc.gap_open, sc.gap_extend)
+        hit = ctx.score(A, B, sc.matrix, sc.gap_open, sc.gap_extend)
     finally:
         ctx.close()
+    return A, B, aln, hit
+
+
+def test_dna_5mbp_pair(oracle_mod, long5m):
+    sc = W.dna_scoring()
+    S, go, ge = sc.matrix, sc.gap_open, sc.gap_extend
+    A, B, aln, hit = long5m
     # the planted window aligns: most of A's 3.75 Mbp core is covered
     assert aln.score > 1_000_000
     assert aln.a_end - aln.a_begin > 3_000_000
@@ -95,3 +104,29 @@ def test_dna_5mbp_pair(oracle_mod):
         assert oracle_mod.nw_score(A[i1:i2], B[j1:j2], S, go, ge) == ps, (i1, j1, i2, j2)
         checked += 1
     assert checked >= 6
+
+
+def test_dna_5mbp_bounded_memory(monkeypatch, long5m):
+    """A 1 GB checkpoint budget takes two checkpoint levels at 5 Mbp: the
+    alignment (score, coordinates, canonical CIGAR) is the one-level one,
+    and the context's device memory after the call stays within the budget
+    plus one band of traceback bits (the one-level run keeps checkpoints
+    every 4,096 rows and columns, about 100 GB)."""
+    import torch
+    from paper_2211_10769_gb300 import binding
+    A, B, want, _ = long5m
+    sc = W.dna_scoring()
+    monkeypatch.setenv("SWGB_CKPT_BUDGET_MB", "1024")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ctx = binding.Context(0)
+    try:
+        got = ctx.align(A, B, sc.matrix, sc.gap_open, sc.gap_extend)
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        ctx.close()
+    assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+        (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end)
+    assert got.cigar == want.cigar
+    used = free0 - free1
+    assert used < (1 << 30) + (4 << 30), used

@@ -332,6 +332,40 @@ def test_align_one_round_limit(ctx, oracle_mod, side):
         (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end, want.cigar)
 
 
+@pytest.mark.parametrize("sides,env", [("3072,1024", {}), ("3072,1024", {"SWGB_P16": "0"}),
+                                       ("4608,1536", {"SWGB_FWD": "12,4,0,2,1"}), ("2048,1024", {})])
+def test_two_level_checkpoints(oracle_mod, monkeypatch, sides, env):
+    """Two levels of checkpoints (forced small sides): the forward fill keeps
+    every BT1-th row and column, each coarse tile the path enters is filled
+    again from them with checkpoints every BT2, and the traceback tiles start
+    from either level.  Paths with long gaps cross coarse tiles in both
+    directions; DNA (packed and int32 forward fills) and protein."""
+    from paper_2211_10769_gb300 import binding
+    monkeypatch.setenv("SWGB_TWO_LEVEL", sides)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    c = binding.Context(0)
+    try:
+        seed = W.BASE_SEED + 9800
+        S = np.full((4, 4), -4, np.int8)
+        np.fill_diagonal(S, 5)
+        cases = [_long_gap_pair(seed, 12000, 3100, 6400, insert=False) + (S, 20, 1),
+                 _long_gap_pair(seed + 10, 11000, 2500, 5200, insert=True) + (S, 12, 1)]
+        A = W.uniform_dna(9000, seed + 20)
+        cases.append((A, W.mutate(A, 4, seed + 21, p_sub=0.1, p_indel=0.02), W.dna_matrix(), 5, 2))
+        P = W.random_protein(7000, seed + 30)
+        p = W.protein_scoring()
+        cases.append((P, W.mutate(P, 20, seed + 31, p_sub=0.25, p_indel=0.03), p.matrix, p.gap_open, p.gap_extend))
+        for a, b, M, o, e in cases:
+            want = oracle_mod.sw_align_ptr(a, b, M, o, e)
+            got = c.align(a, b, M, o, e)
+            assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end) == \
+                (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end), (sides, env, len(a))
+            assert got.cigar == want.cigar, (sides, env, len(a))
+    finally:
+        c.close()
+
+
 def test_kernel_timing(ctx):
     """Per-kernel device time: one forward fill per sw_align, walks and
     traceback fills counted, totals cleared when timing is re-enabled."""

@@ -159,6 +159,25 @@ def test_strip_heights(oracle_mod, monkeypatch, alg, R):
         c.close()
 
 
+@pytest.mark.parametrize("alg", ALGS)
+def test_two_level_checkpoints(oracle_mod, monkeypatch, alg):
+    """Two levels of checkpoints (forced: coarse every 3,072, fine every
+    1,024) with the algorithms' borders on the coarse tiles of the first row
+    and column."""
+    from paper_2211_10769_gb300 import binding
+    monkeypatch.setenv("SWGB_TWO_LEVEL", "3072,1024")
+    c = binding.Context(0)
+    try:
+        seed = W.BASE_SEED + 15800 + alg
+        sc = W.dna_scoring()
+        A = W.uniform_dna(8500, seed)
+        B = np.concatenate([W.uniform_dna(700, seed + 1), W.mutate(A[:7000], 4, seed + 2, p_sub=0.1, p_indel=0.02)])
+        _align_case(c, oracle_mod, A, B, sc.matrix, sc.gap_open, sc.gap_extend, alg)
+        _align_case(c, oracle_mod, B, A, sc.matrix, sc.gap_open, sc.gap_extend, alg)
+    finally:
+        c.close()
+
+
 def test_batch_mixed_algorithms(ctx, oracle_mod):
     """One batch mixing the four algorithms, DNA and protein, empty sides included."""
     from paper_2211_10769_gb300 import binding
