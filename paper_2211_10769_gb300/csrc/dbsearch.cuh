@@ -229,7 +229,7 @@ __device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, c
 }
 
 template <int R, int W, bool OVERSUB>
-__global__ void __launch_bounds__(W * 32, W >= 32 ? 1 : (R >= 12 ? 3 : 4))
+__global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : (R >= 12 ? 3 : 4))
 db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                 const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {

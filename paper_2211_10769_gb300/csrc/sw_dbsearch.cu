@@ -110,10 +110,10 @@ int resident_blocks(sw_ctx *c, int K, int m, int *out) {
 // (144 residues: one 160-row pass at R = 5 instead of 256 rows at R = 8);
 // long ones want R = 16, whose per-step overhead is shared by more rows.
 // Queries whose profile would not leave room for three blocks an SM take
-// blocks of 32 warps (one per SM) at R = 8.
+// blocks of 16 warps (one per SM) at R = 16.
 struct DbShape { int R, W; };
-constexpr DbShape kDbShapes[] = {{4, 8}, {5, 8}, {6, 8}, {8, 8}, {12, 8}, {16, 8}, {8, 32}};
-constexpr int kDbWide = 6;                         // index of the 32-warp shape
+constexpr DbShape kDbShapes[] = {{4, 8}, {5, 8}, {6, 8}, {8, 8}, {12, 8}, {16, 8}, {16, 16}};
+constexpr int kDbWide = 6;                         // index of the one-block-an-SM shape
 constexpr size_t kDbNarrowProfileMax = 96 * 1024;  // profile bytes of a three-blocks-an-SM shape at most
 
 size_t shape_profile_bytes(int s, int K, int m) {
@@ -153,7 +153,7 @@ int swgb::db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out)
         case 3: return resident_blocks<8, 8>(c, K, m, out);
         case 4: return resident_blocks<12, 8>(c, K, m, out);
         case 5: return resident_blocks<16, 8>(c, K, m, out);
-        default: return resident_blocks<8, 32>(c, K, m, out);
+        default: return resident_blocks<16, 16>(c, K, m, out);
     }
 }
 
@@ -175,7 +175,7 @@ int swgb::db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, in
         case 3: return launch_db<8, 8>(c, jobs, njobs, nblocks, D, K, m);
         case 4: return launch_db<12, 8>(c, jobs, njobs, nblocks, D, K, m);
         case 5: return launch_db<16, 8>(c, jobs, njobs, nblocks, D, K, m);
-        default: return launch_db<8, 32>(c, jobs, njobs, nblocks, D, K, m);
+        default: return launch_db<16, 16>(c, jobs, njobs, nblocks, D, K, m);
     }
 }
 

@@ -51,7 +51,7 @@ def test_small_database_all_scores(ctx, oracle_mod):
 
 def test_every_tile_shape(ctx, oracle_mod):
     """Query lengths that pick each tile shape of the packed search (4, 5, 6,
-    8, 12 and 16 rows a lane, and 32-warp blocks for long queries), with one
+    8, 12 and 16 rows a lane, and 16-warp blocks for long queries), with one
     or several passes and the last pass partly padding."""
     sc = W.protein_scoring()
     lengths = (1, 31, 100, 128, 144, 160, 161, 190, 250, 300, 350, 384, 464, 700, 1000, 1500, 4100)
