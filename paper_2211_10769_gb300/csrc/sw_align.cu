@@ -138,6 +138,9 @@ int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int
     }
 }
 
+// Run records of paths up to this many bytes come back with every round's walk state.
+constexpr size_t kRunsEachRoundBytes = 256 * 1024;
+
 // One checkpoint level while its tile side stays within this; two levels above it.
 constexpr long long kMaxOneLevelBT = 16384;
 
@@ -449,10 +452,18 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
     const int HS = tsw * 32 * tbc.R;                     // rows per traceback strip
     const size_t table_cap = (size_t)(band + 1) * (band + 2);
-    RC(c->stage2.ensure(std::max(sizeof(WalkState), table_cap * sizeof(void *))));
-    std::memcpy(c->stage2.p, &w, sizeof(w));
-    CU(cudaMemcpyAsync(c->walk.p, c->stage2.p, sizeof(w), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    // staging: the rounds' tile tables, then the walk's start (its own slot, so that no
+    // synchronisation is needed before the first table is written)
+    const size_t w_off = (table_cap * sizeof(void *) + 15) / 16 * 16;
+    RC(c->stage2.ensure(w_off + sizeof(WalkState)));
+    std::memcpy(static_cast<char *>(c->stage2.p) + w_off, &w, sizeof(w));
+    CU(cudaMemcpyAsync(c->walk.p, static_cast<char *>(c->stage2.p) + w_off, sizeof(w), cudaMemcpyHostToDevice,
+                       c->stream));
+    // short paths: the run records come back with every round's walk state, which saves the
+    // copy (and its synchronisation) after the last round
+    const size_t runs_max = (size_t)(ie + je + 2) * sizeof(int2);
+    const bool runs_each_round = runs_max <= kRunsEachRoundBytes;
+    if (runs_each_round) RC(c->stage3.ensure(128 + runs_max));
 
     // ---- 3. rounds: recompute a band of tiles, walk through it
     const int R = tbc.R;
@@ -536,6 +547,9 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         CU(cudaMemcpyAsync(c->stage3.p, c->walk.p, sizeof(WalkState), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 64, c->err.p, sizeof(int),
                            cudaMemcpyDeviceToHost, c->stream));
+        if (runs_each_round)
+            CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 128, c->runs.p, runs_max, cudaMemcpyDeviceToHost,
+                               c->stream));
         CU(cudaStreamSynchronize(c->stream));
         std::memcpy(&w, c->stage3.p, sizeof(w));
         std::memcpy(&e, static_cast<char *>(c->stage3.p) + 64, sizeof(int));
@@ -545,8 +559,12 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         prev_i = w.i; prev_j = w.j; prev_state = w.state;
     }
     if (w.done != 1) return SW_ECUDA;     // the walk must end at a zero cell or the border
+    if (w.nruns < 0 || (size_t)w.nruns * sizeof(int2) > runs_max) return SW_ECUDA;
 
     // ---- 4. CIGAR text from the run records
+    if (runs_each_round)
+        return finish_alignment(ds.alg, res.x, ie, je, w,
+                                reinterpret_cast<const int2 *>(static_cast<char *>(c->stage3.p) + 128), out);
     std::vector<int2> runs((size_t)w.nruns);
     if (w.nruns > 0) {
         CU(cudaMemcpy(runs.data(), c->runs.p, (size_t)w.nruns * sizeof(int2), cudaMemcpyDeviceToHost));
