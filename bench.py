@@ -62,6 +62,8 @@ def parse():
                     help="comma list of the other workloads to measure after the headline: "
                          "dna2k,variants,dbsearch,batch,serve,dna5m,bounded (default all; 'none' for the headline only)")
     ap.add_argument("--serve-requests", type=int, default=500, help="requests per arrival rate")
+    ap.add_argument("--db-subjects", type=int, default=500_000,
+                    help="subjects of the search database (fewer only for profiling captures)")
     ap.add_argument("--bounded-length", type=int, default=5_000_000,
                     help="length of the long pair aligned under a small checkpoint budget")
     ap.add_argument("--bounded-budget-mb", type=int, default=1024, help="that checkpoint budget (MB)")

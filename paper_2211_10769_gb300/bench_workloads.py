@@ -33,12 +33,13 @@ REPEATS = 20                  # timed runs per measurement: median and mean are 
 _DB_CACHE = {}
 
 
-def _protein_db():
-    """The 500,000-subject database with the five planted queries (generated once)."""
-    if "db" not in _DB_CACHE:
+def _protein_db(nseq=500_000):
+    """The database (500,000 subjects unless a profiling run asks for fewer) with the five
+    planted queries (generated once)."""
+    if nseq not in _DB_CACHE:
         qs = W.protein_queries()
-        _DB_CACHE["db"] = (qs, W.protein_db(500_000, queries=qs))
-    return _DB_CACHE["db"]
+        _DB_CACHE[nseq] = (qs, W.protein_db(nseq, queries=qs))
+    return _DB_CACHE[nseq]
 
 
 def _stats(ts):
@@ -108,7 +109,7 @@ def variants(ctx, torch, stream, args):
 def dbsearch(ctx, torch, stream, args):
     from .binding import Database
     sc = W.protein_scoring()
-    qs, pdb = _protein_db()
+    qs, pdb = _protein_db(args.db_subjects)
     db = Database(ctx, pdb.residues, pdb.offsets)
     total_res = int(pdb.residues.size)
     from .binding import KT_DB16
@@ -176,7 +177,7 @@ def batch(ctx, torch, stream, args):
 def serve(ctx, torch, stream, args):
     from . import binding
     sc = W.protein_scoring()
-    qs, pdb = _protein_db()
+    qs, pdb = _protein_db(args.db_subjects)
     db = binding.Database(ctx, pdb.residues, pdb.offsets)
     total_res = int(pdb.residues.size)
     rates = [float(x) for x in args.serve_rates.split(",")]
