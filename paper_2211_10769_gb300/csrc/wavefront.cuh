@@ -394,7 +394,8 @@ template <int QS, int QB, int IOB, int SHIFT = 0>
 __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
                                                 int n, int go, int K, int Wa, int lag, int2 *ring0,
                                                 uint8_t *bring, int *prod, const int *cons,
-                                                volatile int *s_abort, int lane, int alg = kAlgLocal, int ge = 0)
+                                                volatile int *s_abort, int lane, int alg = kAlgLocal, int ge = 0,
+                                                int *poff = nullptr, int pk1 = 0, int pstride = 0)
 {
     int in_next = 0;
     long long idle = 0;
@@ -417,7 +418,10 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
                     ring0[col & (QS - 1)] = make_int2(v.x - go, v.y);
                 else     // scaled values; -infinity stays far below every real value, without overflow
                     ring0[col & (QS - 1)] = make_int2((v.x - go) * (1 << SHIFT), max(v.y, kNeg >> SHIFT) * (1 << SHIFT));
-                bring[col & (QB - 1)] = (uint8_t)min((int)T.b[col], K);
+                const int c = min((int)T.b[col], K);
+                bring[col & (QB - 1)] = (uint8_t)c;
+                // pair profile (packed fill): the byte offset of the entry for (b[col], b[col - 1])
+                if (poff) poff[col & (QB - 1)] = (c * pk1 + (col > 0 ? min((int)T.b[col - 1], K) : K)) * pstride;
             }
             __syncwarp();
             if (lane == 0) sts_release(&prod[0], target);

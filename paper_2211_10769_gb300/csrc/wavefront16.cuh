@@ -270,6 +270,7 @@ wavefront16_kernel(const FillLaunch L)
     extern __shared__ __align__(16) int8_t prof[];   // p16_profile_bytes
     __shared__ int2 ring[W + 1][QS];                 // (8 (H - open), 8 F), absolute
     __shared__ uint8_t bring[QB];
+    __shared__ int s_poff[PK == kP16Pair ? QB : 1];   // pair profile: byte offset per column (fill_input_warp)
     __shared__ int prod[W + 1];
     __shared__ int cons[W + 1];
     __shared__ long long s_tk;
@@ -336,12 +337,18 @@ wavefront16_kernel(const FillLaunch L)
         // the residue ring's last kP16Pos slots read as padding: lanes compute the columns left
         // of the task (down to -63) during their first two chunks; the input warp reaches those
         // slots only after the last warp has published a column, i.e. left those chunks
-        if (threadIdx.x < kP16Pos) bring[QB - kP16Pos + threadIdx.x] = (uint8_t)K;
+        // bytes per profile entry: pair, per residue combination; int16, per residue
+        const int pstride = PK == kP16Pair ? (R / 4) * NL * 8 : 2 * HC;
+        if (threadIdx.x < kP16Pos) {
+            bring[QB - kP16Pos + threadIdx.x] = (uint8_t)K;
+            if constexpr (PK == kP16Pair) s_poff[QB - kP16Pos + threadIdx.x] = (K * (K + 1) + K) * pstride;
+        }
         __syncthreads();
 
         if (warp == W) {
             fill_input_warp<QS, QB, IOB, kP16Shift>(T, L, strip, tk, n, go, K, Wa, kP16Pos + 1, ring[0], bring,
-                                                    prod, cons, &s_abort, lane);
+                                                    prod, cons, &s_abort, lane, kAlgLocal, 0,
+                                                    PK == kP16Pair ? s_poff : nullptr, K + 1, pstride);
         } else if (warp == W + 1) {
             fill_output_warp<QS, kP16Shift>(T, L, strip, tk, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
         } else if (warp >= Wa) {
@@ -352,8 +359,6 @@ wavefront16_kernel(const FillLaunch L)
             const int grow = rbase + g * R;
             // this lane's profile base (pair: its first chunk of combination 0; int16: its rows)
             const int8_t *prow = PK == kP16Pair ? prof + g * 8 : prof + 2 * g * R;
-            // bytes per profile entry: pair, per residue combination; int16, per residue
-            const int pstride = PK == kP16Pair ? (R / 4) * NL * 8 : 2 * HC;
             const unsigned ngo2 = p16_pack(-8 * go, -8 * go), nge2 = p16_pack(-8 * ge, -8 * ge);
             const unsigned neg2 = p16_pack(kNeg16p, kNeg16p);
             P16Lane<R> st;
@@ -370,7 +375,6 @@ wavefront16_kernel(const FillLaunch L)
             int2 *rout = ring[warp + 1];
             int seen_in = 0;
             bool loaded = false;
-            int cprev = K;                 // the bottom half's residue (left of the task: padding)
             uint32_t pw[R / 2], pwp[R / 2];
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);
@@ -393,9 +397,9 @@ wavefront16_kernel(const FillLaunch L)
                 if (ring_hi > 0 && !warp_wait_geq(&cons[warp + 1], ring_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
                 if (!loaded) {
                     const int c = min((int)bring[(s0 - 2 * lane) & (QB - 1)], K);
-                    if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (c * (K + 1) + cprev) * pstride, pw);
+                    // (the sweep's first step: the bottom halves' column is left of the task, padding)
+                    if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (c * (K + 1) + K) * pstride, pw);
                     else p16_load<R, PK, NL>(prow + c * pstride, pw);
-                    cprev = c;
                     loaded = true;
                 }
                 {   // new lane base from the top half's first row at its last column; the best
@@ -439,15 +443,17 @@ wavefront16_kernel(const FillLaunch L)
 #pragma unroll UNR
                     for (int k = 0; k < CH; ++k) {
                         const int s = s0 + k;
-                        const int cn = min((int)bring[(s + 1 - 2 * lane) & (QB - 1)], K);
                         const uint2 topn = s_top[warp][(k + 1) & (CH - 1)];   // (unused after the last step)
                         uint32_t pwn[R / 2];
-                        if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (cn * (K + 1) + cprev) * pstride, pwn);
-                        else p16_load<R, PK, NL>(prow + cn * pstride, pwn);
+                        if constexpr (PK == kP16Pair) {
+                            p16_load<R, PK, NL>(prow + s_poff[(s + 1 - 2 * lane) & (QB - 1)], pwn);
+                        } else {
+                            const int cn = min((int)bring[(s + 1 - 2 * lane) & (QB - 1)], K);
+                            p16_load<R, PK, NL>(prow + cn * pstride, pwn);
+                        }
                         p16_step<R, PK, QS, false>(st, pw, pwp, top, s, lane, n, nge2, ngo2, neg2, rout);
 #pragma unroll
                         for (int q = 0; q < R / 2; ++q) { pwp[q] = pw[q]; pw[q] = pwn[q]; }
-                        cprev = cn;
                         top = topn;
                     }
                 } else {
@@ -464,12 +470,15 @@ wavefront16_kernel(const FillLaunch L)
                             const int cn = jn < n ? min((int)bring[jn & (QB - 1)], K) : K;
                             const uint2 topn = s_top[warp][(gs + k + 1) & (CH - 1)];
                             uint32_t pwn[R / 2];
-                            if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (cn * (K + 1) + cprev) * pstride, pwn);
-                            else p16_load<R, PK, NL>(prow + cn * pstride, pwn);
+                            if constexpr (PK == kP16Pair) {   // the bottom half's residue: column jn - 1
+                                const int cb = jn - 1 < n ? min((int)bring[(jn - 1) & (QB - 1)], K) : K;
+                                p16_load<R, PK, NL>(prow + (cn * (K + 1) + cb) * pstride, pwn);
+                            } else {
+                                p16_load<R, PK, NL>(prow + cn * pstride, pwn);
+                            }
                             p16_step<R, PK, QS, true>(st, pw, pwp, top, s, lane, n, nge2, ngo2, neg2, rout);
 #pragma unroll
                             for (int q = 0; q < R / 2; ++q) { pwp[q] = pw[q]; pw[q] = pwn[q]; }
-                            cprev = cn;
                             top = topn;
                         }
                     }
