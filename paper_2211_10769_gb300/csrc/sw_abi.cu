@@ -337,7 +337,6 @@ int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
     L.total = tickets;
     L.spin_limit = c->spin_limit;
     L.ntasks = (int)tasks.size();
-    L.pace_permille = c->pace_permille;
     // c->stage is pinned and copied asynchronously: callers synchronise the
     // stream before they run another fill (every ABI call ends with a sync).
     return launch_fill(c, cfg, mode, fold, L, K, tickets);
@@ -433,7 +432,6 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     if (const char *f = std::getenv("SWGB_ONE_ROUND")) c->one_round = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_TWO_LEVEL")) std::sscanf(f, "%lld,%lld", &c->two_level_bt1, &c->two_level_bt2);
     if (const char *f = std::getenv("SWGB_P16")) c->p16 = std::atoi(f) != 0;
-    if (const char *f = std::getenv("SWGB_PACE")) c->pace_permille = std::max(0, std::atoi(f));
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
     if (const char *f = std::getenv("SWGB_TB_SW")) c->tb_strip_warps = std::atoi(f);
     // checkpoint memory of sw_align: 40% of the device memory free now (at least 4 GB), so that

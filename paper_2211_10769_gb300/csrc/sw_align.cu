@@ -278,7 +278,6 @@ int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, 
     L.total = t.nstrips;
     L.spin_limit = c->spin_limit;
     L.ntasks = 1;
-    L.pace_permille = c->pace_permille;
     RC(launch_fill(c, fwd, kModeScore, fold, L, ds.K, t.nstrips));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(dtasks, 1, static_cast<const int4 *>(c->cand.p),
                                                        static_cast<const DevScoring *>(c->scorings.p),

@@ -82,7 +82,7 @@ struct sw_batch {
     std::vector<DevScoring> scorings;
     const uint8_t *da = nullptr, *db = nullptr;    // residues on the device
     std::vector<int64_t> aoff, boff;
-    DevBuf a_own, b_own, tasks, prog, cand, res, hits, perm, bnd, ticket, meta;
+    DevBuf a_own, b_own, tasks, prog, cand, res, hits, perm, bnd, ticket, meta, order;
     HostBuf host_hits;
     std::vector<Bin> bins;
     FillConfig cfg{8, 4};          // the tile shape of the bin with the most cells
@@ -154,6 +154,18 @@ int build_plan(sw_batch *B) {
         bases.push_back(bin.tbase);
         if (cells > best_cells) { best_cells = cells; B->cfg = bin.cfg; }
     }
+    // claim order: within a bin, every task's first strip (largest task first), then every second
+    // strip, and so on.  In task order a block that takes a task's strip k waits until strip k - 1
+    // has produced rows, holding its SM slot idle; level by level, strip k - 1 has run ahead.
+    std::vector<int2> claims((size_t)std::max<long long>(1, tickets));
+    for (const Bin &bin : B->bins) {
+        long long pos = bin.tbase;
+        int levels = 0;
+        for (int k = 0; k < bin.nt; ++k) levels = std::max(levels, tasks[(size_t)(bin.t0 + k)].nstrips);
+        for (int lvl = 0; lvl < levels; ++lvl)
+            for (int k = 0; k < bin.nt; ++k)
+                if (lvl < tasks[(size_t)(bin.t0 + k)].nstrips) claims[(size_t)pos++] = make_int2(k, lvl);
+    }
     B->ntasks = (int)tasks.size();
     B->tickets = tickets;
     const size_t tb = std::max<size_t>(1, tasks.size()) * sizeof(FillTask);
@@ -162,12 +174,14 @@ int build_plan(sw_batch *B) {
     RC(B->cand.ensure(std::max<long long>(1, tickets) * sizeof(int4)));
     RC(B->res.ensure(std::max<size_t>(1, tasks.size()) * sizeof(int4)));
     RC(B->perm.ensure(std::max<size_t>(1, order.size()) * sizeof(int32_t)));
+    RC(B->order.ensure(claims.size() * sizeof(int2)));
     // counters and error word: [bins x u64 counters][bins x i64 bases][err]
     const size_t nb = std::max<size_t>(1, B->bins.size());
     RC(B->ticket.ensure(16 * nb + 256));
     if (!tasks.empty()) {
         CU(cudaMemcpy(B->tasks.p, tasks.data(), tb, cudaMemcpyHostToDevice));
         CU(cudaMemcpy(B->perm.p, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(B->order.p, claims.data(), claims.size() * sizeof(int2), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(static_cast<char *>(B->ticket.p) + 8 * nb, bases.data(), bases.size() * sizeof(long long),
                       cudaMemcpyHostToDevice));
     }
@@ -213,6 +227,7 @@ int enqueue_run(sw_batch *B) {
                 L.total = bin.tbase + bin.tcount;
                 L.spin_limit = c->spin_limit;
                 L.ntasks = bin.nt;
+                L.order = static_cast<const int2 *>(B->order.p);
                 c->stream = bs;
                 rc = launch_fill(c, bin.cfg, kModeScore, fold_open(sc), L, sc.K, bin.tcount);
                 c->stream = saved;

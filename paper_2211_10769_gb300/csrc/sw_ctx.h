@@ -75,7 +75,6 @@ struct sw_ctx {
     swgb::FillConfig bat{8, 4};       // batches of pairs (unless autotuned)
     bool prof32 = true;               // int32 query profiles where they fit (small alphabets)
     bool p16 = true;                  // packed 16-bit pair fill where it is exact (p16_fits)
-    int pace_permille = 0;            // slow-down of a strip chain's first warp (FillLaunch; off: measured no gain)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
     bool one_round = false;           // sw_align of small pairs in one round (whole-matrix traceback bits)
     long long two_level_bt1 = 0;      // sw_align: forced coarse / fine checkpoint sides (0 = by budget)

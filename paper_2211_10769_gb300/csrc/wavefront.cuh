@@ -97,7 +97,12 @@ struct FillLaunch {
     long long total;              // total tickets
     long long spin_limit;         // polls before a wait gives up
     int ntasks;
-    int pace_permille;            // slow-down of a long strip chain's first warp (0 = none)
+    // claim order (optional): claim k takes strip order[k].y of task order[k].x, so that a
+    // plan can hand out every task's first strip before any second one; nullptr: tickets in
+    // task order, each task's strips consecutive (task = last with ticket0 <= k).  Either way a
+    // strip's predecessor is claimed before it, and progress and candidates are kept per
+    // (task, strip) at ticket0 + strip.
+    const int2 *order;
 };
 
 template <int R> struct TbWord;
@@ -164,6 +169,28 @@ __device__ __forceinline__ int lds_acquire(const int *p) {
 
 __device__ __forceinline__ void sts_release(int *p, int v) {
     asm volatile("st.release.cta.shared.b32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+// Thread 0 of a fill block claims its next strip: *s_tk = the claim (L.total once all are taken
+// or after an error), and the task and strip it stands for (FillLaunch::order).
+__device__ __forceinline__ void claim_strip(const FillLaunch &L, long long *s_tk, int *s_task, int *s_strip) {
+    long long tk = (long long)atomicAdd(L.ticket, 1ULL);
+    if (ld_volatile(L.err) != 0) tk = L.total;           // stop early after an error
+    *s_tk = tk;
+    if (tk >= L.total) return;
+    if (L.order) {
+        const int2 o = L.order[tk];
+        *s_task = o.x;
+        *s_strip = o.y;
+        return;
+    }
+    int lo = 0, hi = L.ntasks - 1;                       // last task with ticket0 <= tk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.tasks[mid].ticket0 <= tk) lo = mid; else hi = mid - 1;
+    }
+    *s_task = lo;
+    *s_strip = (int)(tk - L.tasks[lo].ticket0);
 }
 
 // The warp waits until *ctr >= want (bounded).  Every lane reads the counter
@@ -391,7 +418,7 @@ __device__ __forceinline__ void split_staircase_prologue(const FillTask &T, Lane
 // last active warp (whose lanes read furthest back, `lag` columns behind its
 // published count) has published.
 template <int QS, int QB, int IOB, int SHIFT = 0>
-__device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
+__device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLaunch &L, int strip, long long slot,
                                                 int n, int go, int K, int Wa, int lag, int2 *ring0,
                                                 uint8_t *bring, int *prod, const int *cons,
                                                 volatile int *s_abort, int lane, int alg = kAlgLocal, int ge = 0,
@@ -400,7 +427,7 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
     int in_next = 0;
     long long idle = 0;
     const int2 *src = strip == 0 ? T.top : T.bnd + (size_t)((strip - 1) % T.nslot) * n;
-    const int *pprev = L.prog + (tk - 1);
+    const int *pprev = L.prog + (slot - 1);
     int avail_prev = strip == 0 ? n : 0;
     while (in_next < n) {
         const int room0 = lds_acquire(&cons[0]) + QS;
@@ -454,7 +481,7 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
 // strip's input and, every ckpt_every-th strip, a checkpoint row -- and
 // publishes the stored column count with a release store.
 template <int QS, int SHIFT = 0>
-__device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLaunch &L, int strip, long long tk,
+__device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLaunch &L, int strip, long long slot,
                                                  int n, int go, int SH, int Wa, const int2 *ringW,
                                                  const int *prod, int *cons, volatile int *s_abort, int lane)
 {
@@ -483,7 +510,7 @@ __device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLa
             // barrier; the release (gpu scope) publishes them cumulatively
             __syncwarp();
             if (lane == 0) {
-                if (store) st_release(L.prog + tk, avail_out);
+                if (store) st_release(L.prog + slot, avail_out);
                 sts_release(&cons[Wa], avail_out);
             }
             out_next = avail_out;
@@ -525,7 +552,7 @@ wavefront_kernel(const FillLaunch L)
     __shared__ int prod[W + 1];                      // columns available in channel k
     __shared__ int cons[W + 1];                      // columns consumed from channel k
     __shared__ long long s_tk;
-    __shared__ int s_task;
+    __shared__ int s_task, s_strip;
     __shared__ volatile int s_abort;
     __shared__ int4 s_cand[W];
 
@@ -534,18 +561,8 @@ wavefront_kernel(const FillLaunch L)
 
     for (;;) {
         if (threadIdx.x == 0) {
-            long long tk = (long long)atomicAdd(L.ticket, 1ULL);
-            if (ld_volatile(L.err) != 0) tk = L.total;       // stop early after an error
-            s_tk = tk;
+            claim_strip(L, &s_tk, &s_task, &s_strip);
             s_abort = 0;
-            if (tk < L.total) {
-                int lo = 0, hi = L.ntasks - 1;               // last task with ticket0 <= tk
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (L.tasks[mid].ticket0 <= tk) lo = mid; else hi = mid - 1;
-                }
-                s_task = lo;
-            }
         }
         if (threadIdx.x <= W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
         __syncthreads();
@@ -554,7 +571,8 @@ wavefront_kernel(const FillLaunch L)
         const FillTask &T = L.tasks[s_task];
         const DevScoring &SC = L.scorings[T.scoring];
         const int K = SC.K, go = SC.go, ge = SC.ge;
-        const int strip = (int)(tk - T.ticket0);
+        const int strip = s_strip;
+        const long long slot = T.ticket0 + strip;        // progress and candidate of (task, strip)
         const int SW = (T.strip_warps > 0 && T.strip_warps < W) ? T.strip_warps : W;
         const int SH = SW * 32 * R;                     // rows per strip of this task
         const int rbase = strip * SH;                   // first row of the strip within the task
@@ -582,11 +600,11 @@ wavefront_kernel(const FillLaunch L)
 
         if (warp == W) {
             // ================= input warp: top boundary row and residues =================
-            fill_input_warp<QS, QB, IOB>(T, L, strip, tk, n, go, K, Wa, 64, ring[0], bring, prod, cons,
+            fill_input_warp<QS, QB, IOB>(T, L, strip, slot, n, go, K, Wa, 64, ring[0], bring, prod, cons,
                                          &s_abort, lane, LOCAL ? kAlgLocal : SC.alg, ge);
         } else if (warp == W + 1) {
             // ================= output warp: bottom row to global memory =================
-            fill_output_warp<QS>(T, L, strip, tk, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
+            fill_output_warp<QS>(T, L, strip, slot, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
         } else if (warp >= Wa) {
             if constexpr (MODE != kModeTb)
                 if (lane == 0) s_cand[warp] = make_int4(LOCAL ? 0 : kNoScore, 0x7fffffff, 0x7fffffff, 0);
@@ -800,7 +818,7 @@ wavefront_kernel(const FillLaunch L)
                     if (cand_better(o.x, o.z, o.y, b.x, b.z, b.y)) b = o;
                 }
                 b.w = LOCAL ? (b.x > 0 ? 1 : 0) : (b.x != kNoScore ? 1 : 0);
-                L.cand[tk] = b;
+                L.cand[slot] = b;
             }
         }
         __syncthreads();

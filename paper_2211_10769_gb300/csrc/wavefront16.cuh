@@ -246,10 +246,13 @@ __device__ __forceinline__ uint2 p16_top_row(int2 v, int B0, int ge8) {
     return make_uint2((unsigned)tu << 16, (unsigned)tf << 16);
 }
 
+// Steps per unrolled body of the steady loop, measured on GB300 (2, 4, 8, 16, 32 at 12 rows a lane): 8 for
+// the score fill; 16 with checkpoints above 8 rows a lane (its chunk-end code runs once per 16 steps); 32
+// is much slower (a body that large no longer stays in the instruction cache).
 #ifndef SWGB_P16_UNROLL
-constexpr int fill16_unroll(int R) { return R <= 8 ? 8 : 16; }   // measured on GB300 (2, 4, 8, 16)
+constexpr int fill16_unroll(int R, int MODE) { return (R <= 8 || MODE == kModeScore) ? 8 : 16; }
 #else
-constexpr int fill16_unroll(int) { return SWGB_P16_UNROLL; }
+constexpr int fill16_unroll(int, int) { return SWGB_P16_UNROLL; }
 #endif
 
 template <int R, int W, int MODE, int PK>
@@ -264,7 +267,7 @@ wavefront16_kernel(const FillLaunch L)
     constexpr int CH = kP16CH, QS = kP16QS, QB = kQB, IOB = kIOB;
     constexpr int LAG = kP16Pos - 1;                 // lane 31's bottom half trails lane 0's top half
     static_assert(QS >= 2 * IOB + 2 * CH + 2 * kP16Pos, "ring too small");
-    constexpr int UNR = fill16_unroll(R);
+    constexpr int UNR = fill16_unroll(R, MODE);
     static_assert(CH % UNR == 0, "chunks are whole unrolled groups");
 
     extern __shared__ __align__(16) int8_t prof[];   // p16_profile_bytes
@@ -274,7 +277,7 @@ wavefront16_kernel(const FillLaunch L)
     __shared__ int prod[W + 1];
     __shared__ int cons[W + 1];
     __shared__ long long s_tk;
-    __shared__ int s_task;
+    __shared__ int s_task, s_strip;
     __shared__ volatile int s_abort;
     __shared__ int4 s_cand[W];
     __shared__ uint2 s_top[W][CH];                   // lane 0's rows above for one chunk (p16_top_row)
@@ -285,18 +288,8 @@ wavefront16_kernel(const FillLaunch L)
 
     for (;;) {
         if (threadIdx.x == 0) {
-            long long tk = (long long)atomicAdd(L.ticket, 1ULL);
-            if (ld_volatile(L.err) != 0) tk = L.total;       // stop early after an error
-            s_tk = tk;
+            claim_strip(L, &s_tk, &s_task, &s_strip);
             s_abort = 0;
-            if (tk < L.total) {
-                int lo = 0, hi = L.ntasks - 1;               // last task with ticket0 <= tk
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (L.tasks[mid].ticket0 <= tk) lo = mid; else hi = mid - 1;
-                }
-                s_task = lo;
-            }
         }
         if (threadIdx.x <= W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
         __syncthreads();
@@ -305,7 +298,8 @@ wavefront16_kernel(const FillLaunch L)
         const FillTask &T = L.tasks[s_task];
         const DevScoring &SC = L.scorings[T.scoring];
         const int K = SC.K, go = SC.go, ge = SC.ge;
-        const int strip = (int)(tk - T.ticket0);
+        const int strip = s_strip;
+        const long long slot = T.ticket0 + strip;        // progress and candidate of (task, strip)
         const int SW = (T.strip_warps > 0 && T.strip_warps < W) ? T.strip_warps : W;
         const int SH = SW * 32 * R;
         const int rbase = strip * SH;
@@ -346,11 +340,11 @@ wavefront16_kernel(const FillLaunch L)
         __syncthreads();
 
         if (warp == W) {
-            fill_input_warp<QS, QB, IOB, kP16Shift>(T, L, strip, tk, n, go, K, Wa, kP16Pos + 1, ring[0], bring,
+            fill_input_warp<QS, QB, IOB, kP16Shift>(T, L, strip, slot, n, go, K, Wa, kP16Pos + 1, ring[0], bring,
                                                     prod, cons, &s_abort, lane, kAlgLocal, 0,
                                                     PK == kP16Pair ? s_poff : nullptr, K + 1, pstride);
         } else if (warp == W + 1) {
-            fill_output_warp<QS, kP16Shift>(T, L, strip, tk, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
+            fill_output_warp<QS, kP16Shift>(T, L, strip, slot, n, go, SH, Wa, ring[Wa], prod, cons, &s_abort, lane);
         } else if (warp >= Wa) {
             if (lane == 0) s_cand[warp] = make_int4(0, 0x7fffffff, 0x7fffffff, 0);
         } else {
@@ -379,14 +373,7 @@ wavefront16_kernel(const FillLaunch L)
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);
             uint2 top;
-            // the head of a long strip chain (warp 0 of strip 0) runs a little slower than it
-            // could (L.pace_permille of its chunk time), so that every warp after it has slack
-            // and catches up after a slow chunk instead of keeping the delay: without it each
-            // warp's lag behind the one above grows over the sweep, by ~4 us per warp measured
-            // over 200,000 columns, and the chain's drain with it
-            const bool pace = L.pace_permille > 0 && strip == 0 && warp == 0 && T.nstrips >= 8;
             for (int s0 = 0; s0 < n + LAG; s0 += CH) {
-                const long long pc0 = pace ? clock64() : 0;
                 const int need_in = min(n, s0 + CH + 1);
                 if (need_in > seen_in) {
                     if (!warp_wait_geq(&prod[warp], need_in, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
@@ -505,10 +492,6 @@ wavefront16_kernel(const FillLaunch L)
                         next_ck += T.colck_every;
                     }
                 }
-                if (pace) {
-                    const long long until = clock64() + (clock64() - pc0) * L.pace_permille / 1000;
-                    while (clock64() < until) { }
-                }
                 __syncwarp();
                 if (lane == 0) {
                     sts_release(&cons[warp], min(n, s0 + CH));
@@ -546,7 +529,7 @@ wavefront16_kernel(const FillLaunch L)
                 if (cand_better(o.x, o.z, o.y, b.x, b.z, b.y)) b = o;
             }
             b.w = b.x > 0 ? 1 : 0;
-            L.cand[tk] = b;
+            L.cand[slot] = b;
         }
         __syncthreads();
     }
