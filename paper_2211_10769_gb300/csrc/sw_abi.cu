@@ -267,7 +267,11 @@ FillConfig swgb::pair_fill_config_for(const sw_ctx *c, int64_t rows, const DevSc
         f.P16 = f.P16 && p16_fits(s, f.R) && f.W == 4;
         return f;
     }
-    if (c->p16) {
+    // Up to one 512-row strip per SM the int32 fill's 4-row lanes use twice the SMs of the packed
+    // fill's 8-row lanes, which outweighs the packed fill's cheaper cells (2 kbp: 0.170 against
+    // 0.190 ms); above that both take the same SM count and the packed fill wins (200 kbp: 19.8
+    // against 24.0 ms)
+    if (c->p16 && rows > (int64_t)c->nsm * 4 * 32 * 4) {
         for (int R : {8, 12, 16}) {
             const int64_t sh = 4LL * 32 * R;
             if ((rows + sh - 1) / sh <= (int64_t)c->nsm || R == 16) {

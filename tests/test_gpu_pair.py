@@ -19,14 +19,19 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 @pytest.fixture(scope="module", params=["packed16", "int32", "one_round"])
 def ctx(request):
-    """A context on the packed 16-bit pair fill (the default where it is
-    exact), one restricted to the int32 fill, and one that reconstructs
-    small pairs in one round (whole-matrix traceback bits) instead of through
-    checkpoints and bands of traceback tiles: every test runs on all three."""
+    """A context on the packed 16-bit pair fill (forced at 8 rows a lane
+    wherever it is exact), one restricted to the int32 fill, and one that
+    reconstructs small pairs in one round (whole-matrix traceback bits)
+    instead of through checkpoints and bands of traceback tiles: every test
+    runs on all three."""
     from paper_2211_10769_gb300 import binding, build
     build.build()
+    # packed16: the packed fill forced at 8 rows a lane (by default pairs up to 152 x 512 rows take
+    # the int32 fill, which has more SMs to use there)
     env = {"SWGB_P16": "0" if request.param == "int32" else "1",
            "SWGB_ONE_ROUND": "1" if request.param == "one_round" else "0"}
+    if request.param == "packed16":
+        env["SWGB_FWD"] = "8,4,0,2,1"
     old = {k: os.environ.get(k) for k in env}
     os.environ.update(env)
     try:
