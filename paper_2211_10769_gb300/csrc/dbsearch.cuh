@@ -11,7 +11,10 @@
 // the subjects' columns exactly as in the pairwise fill (bottom H / F to the
 // next lane by shuffle), and longer queries take several passes, the bottom
 // row of one pass feeding the next through a per-warp boundary row in
-// global memory.  The query profile (int8, S + open, all passes) sits in
+// global memory.  Short queries may instead run two independent 16-lane
+// wavefronts per warp (G = 16), each over its own pair of subjects, so that a
+// lane holds more rows of a short query and the skew of a wavefront is 15
+// steps rather than 31.  The query profile (int8, S + open, all passes) sits in
 // shared memory; the two residues' score bytes are merged into one packed
 // register with a single prmt.  The cell update is the pairwise one in
 // __viaddmax_s16x2 / __viaddmax_s16x2_relu form.
@@ -175,17 +178,18 @@ struct DbLane {
     const int8_t *prow;          // this lane's profile rows of the current pass
 };
 
-// One step of the packed fill: column j = s - lane of both subjects.  CHECK
-// handles columns outside the pair (the first and last 31 steps).
-template <int R, bool CHECK>
-__device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, const uint16_t *pr, uint2 *bnd,
+// One step of the packed fill: column j = s - gl of both subjects, gl = the
+// lane's index in its wavefront of G lanes.  CHECK handles columns outside the
+// pair (the first and last G - 1 steps).
+template <int R, int G, bool CHECK>
+__device__ __forceinline__ void db_step(DbLane<R> &st, int s, int gl, int n, const uint16_t *pr, uint2 *bnd,
                                         bool tops, bool last, int K, int mpad,
                                         unsigned nge2, unsigned ngo2, unsigned neg2)
 {
-    const int j = s - lane;
-    unsigned uup = __shfl_up_sync(kFull, st.ub, 1);
-    unsigned fup = __shfl_up_sync(kFull, st.fb, 1);
-    if (lane == 0) { uup = st.topv.x; fup = st.topv.y; }
+    const int j = s - gl;
+    unsigned uup = __shfl_up_sync(kFull, st.ub, 1, G);
+    unsigned fup = __shfl_up_sync(kFull, st.fb, 1, G);
+    if (gl == 0) { uup = st.topv.x; fup = st.topv.y; }
     // inputs of the next step
     const int jn = j + 1;
     unsigned cpn;
@@ -222,17 +226,19 @@ __device__ __forceinline__ void db_step(DbLane<R> &st, int s, int lane, int n, c
 #pragma unroll
         for (int r = 0; r + 1 < R; r += 2) st.cmax = __vimax3_s16x2(st.cmax, st.U[r], st.U[r + 1]);
         if constexpr (R % 2 == 1) st.cmax = __vimax3_s16x2(st.cmax, st.U[R - 1], st.U[R - 1]);
-        if (!last && lane == 31) bnd[j] = make_uint2(st.ub, st.fb);
+        if (!last && gl == G - 1) bnd[j] = make_uint2(st.ub, st.fb);
     }
     st.cp = cpn;
     st.topv = topn;
 }
 
-template <int R, int W, bool OVERSUB>
+template <int R, int W, bool OVERSUB, int G = 32>
 __global__ void __launch_bounds__(W * 32, W >= 16 ? 1 : (R >= 12 ? 3 : 4))
 db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
                 const DevScoring *__restrict__ scorings, uint2 *__restrict__ scratch)
 {
+    static_assert(G == 32 || G == 16, "one or two wavefronts a warp");
+    constexpr int NG = 32 / G;                    // wavefronts (pairs of subjects) a warp
     extern __shared__ __align__(16) int8_t prof[];
     // OVERSUB: the grid may exceed the blocks that fit at once (the server's steps); blocks
     // beyond the first wave share the scratch slots
@@ -253,8 +259,8 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
     const DevScoring &SC = scorings[J.scoring];
     const int K = SC.K, go = SC.go, ge = SC.ge;
     const int m = J.m;
-    constexpr int ROWS = 32 * R;
-    constexpr int LS = db_lane_slot(R), PROWS = 32 * LS;   // profile bytes per lane and per pass
+    constexpr int ROWS = G * R;
+    constexpr int LS = db_lane_slot(R), PROWS = G * LS;    // profile bytes per lane and per pass
     const int passes = (m + ROWS - 1) / ROWS;
     const int mpad = passes * PROWS;
     for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
@@ -270,23 +276,44 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
     for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
     const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
     const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1), grp = lane / G;          // the lane's wavefront and its place there
     const int gwarp = slot * W + (threadIdx.x >> 5);
-    uint2 *bnd = scratch + (size_t)gwarp * (size_t)(D.maxlen + 1);
+    uint2 *bnd = scratch + ((size_t)gwarp * NG + grp) * (size_t)(D.maxlen + 1);
     const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
     const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
 
     for (;;) {
-        int p = 0;
-        if (lane == 0) p = J.pair0 + atomicAdd(J.next_pair, 1) * J.pair_stride;
-        p = __shfl_sync(kFull, p, 0);
-        if (p >= J.pair1) break;
-        const int sa = D.pairs[2 * p], sb = D.pairs[2 * p + 1];
-        const uint16_t *pr = D.pres + D.poff[p];
-        const int n = (int)(D.poff[p + 1] - D.poff[p]) - 1;     // columns (pr[n]: padding)
+        // the warp takes NG consecutive pairs (similar lengths: the pairs are sorted), one per wavefront
+        int base = 0;
+        if (lane == 0) base = atomicAdd(J.next_pair, NG);
+        base = __shfl_sync(kFull, base, 0);
+        const int p = J.pair0 + (base + grp) * J.pair_stride;
+        const bool live = p < J.pair1;
+        if constexpr (NG == 1) {
+            if (!live) break;
+        } else {
+            if (!__any_sync(kFull, live)) break;
+        }
+        // a wavefront without a pair steps through no columns (its lanes still take part in the
+        // warp's shuffles); its residue pointer only has to be readable
+        int sa = -1, sb = -1, n = 0;
+        const uint16_t *pr = D.pres;
+        if (NG == 1 || live) {
+            sa = D.pairs[2 * p];
+            sb = D.pairs[2 * p + 1];
+            pr = D.pres + D.poff[p];
+            n = (int)(D.poff[p + 1] - D.poff[p]) - 1;           // columns (pr[n]: padding)
+        }
+        int nmax = n, nmin = n;                                  // over the warp's wavefronts
+        if constexpr (NG > 1) {
+            const int o = __shfl_xor_sync(kFull, n, G);
+            nmax = max(n, o);
+            nmin = min(n, o);
+        }
         unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
         for (int pass = 0; pass < passes; ++pass) {
             DbLane<R> st;
-            st.prow = prof + pass * PROWS + lane * LS;
+            st.prow = prof + pass * PROWS + gl * LS;
 #pragma unroll
             for (int r = 0; r < R; ++r) { st.U[r] = ngo2; st.E[r] = neg2; }
             st.ub = ngo2; st.fb = neg2; st.udiag0 = ngo2;
@@ -294,31 +321,31 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
             const bool last = pass + 1 == passes;
             const bool tops = pass > 0;
             // prefetched inputs of this lane's first column and of lane 0's first top cell
-            st.cp = lane == 0 && n > 0 ? pr[0] : 0xffffu;
+            st.cp = gl == 0 && n > 0 ? pr[0] : 0xffffu;
             st.topv = (tops && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
-            for (int s0 = 0; s0 < n + 31; s0 += kDbCH) {
-                if (s0 >= 31 && s0 + kDbCH <= n) {
-                    // steady state: every lane's column is inside the pair, the prefetched
+            for (int s0 = 0; s0 < nmax + G - 1; s0 += kDbCH) {
+                if (s0 >= G - 1 && s0 + kDbCH <= nmin) {
+                    // steady state: every lane's column is inside its pair, the prefetched
                     // column at most the padding column n
 #pragma unroll
                     for (int k = 0; k < kDbCH; ++k)
-                        db_step<R, false>(st, s0 + k, lane, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+                        db_step<R, G, false>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
                 } else {
-                    for (int k = 0; k < kDbCH && s0 + k < n + 31; ++k)
-                        db_step<R, true>(st, s0 + k, lane, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+                    for (int k = 0; k < kDbCH && s0 + k < nmax + G - 1; ++k)
+                        db_step<R, G, true>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
                 }
             }
             cmax = st.cmax;
             __syncwarp();
         }
-        // warp maximum of each half
+        // each wavefront's maximum of each half
         int ma = lo16(cmax), mb = hi16(cmax);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int off = G / 2; off > 0; off >>= 1) {
             ma = max(ma, __shfl_xor_sync(kFull, ma, off));
             mb = max(mb, __shfl_xor_sync(kFull, mb, off));
         }
-        if (lane == 0) {
+        if (gl == 0 && (NG == 1 || live)) {
             const int outs[2] = {sa, sb};
             const int mx[2] = {ma, mb};
             for (int h = 0; h < 2; ++h) {

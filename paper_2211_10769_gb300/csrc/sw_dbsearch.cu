@@ -8,6 +8,7 @@
 #include "aux_kernels.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -41,22 +42,22 @@ static __global__ void max_code_kernel(const uint8_t *s, long long len, int *out
 
 constexpr long long kMaxProfileSmem = 200 * 1024;
 
-// Profile bytes of a query of m residues for tile shape R (whole passes of
-// 32 lane slots of db_lane_slot(R) bytes, per residue code and padding).
-template <int R>
+// Profile bytes of a query of m residues for tile shape (R, G) (whole passes
+// of G lane slots of db_lane_slot(R) bytes, per residue code and padding).
+template <int R, int G>
 size_t db_profile_bytes(int K, int m) {
-    constexpr int ROWS = 32 * R;
-    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * 32 * db_lane_slot(R);
+    constexpr int ROWS = G * R;
+    const long long mpad = (long long)((m + ROWS - 1) / ROWS) * G * db_lane_slot(R);
     return (size_t)(K + 1) * (size_t)mpad;
 }
 
-template <int R, int W>
+template <int R, int W, int G>
 int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m) {
-    const size_t smem = db_profile_bytes<R>(K, m);
+    const size_t smem = db_profile_bytes<R, G>(K, m);
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false>, W * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false, G>, W * 32, smem));
     int occ2 = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, db_s16x2_kernel<R, W, true>, W * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, db_s16x2_kernel<R, W, true, G>, W * 32, smem));
     occ = std::min(occ, occ2);
     if (occ < 1) return SW_ECUDA;
     // boundary rows: one per warp of every block that can be resident at once; a grid larger
@@ -65,7 +66,8 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     D.nslots = occ * c->nsm;
     D.slot_words = (D.nslots + 31) / 32;
     const bool over = nblocks > D.nslots;
-    RC(c->dbscratch.ensure((size_t)D.nslots * W * (size_t)(D.maxlen + 1) * sizeof(uint2)));
+    // (one boundary row per wavefront: 32 / G of them a warp)
+    RC(c->dbscratch.ensure((size_t)D.nslots * W * (32 / G) * (size_t)(D.maxlen + 1) * sizeof(uint2)));
     RC(c->dbslots.ensure((size_t)D.slot_words * sizeof(unsigned)));
     D.slot_pool = static_cast<unsigned *>(c->dbslots.p);
     D.err = static_cast<int *>(c->err.p);
@@ -75,7 +77,7 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
         CU(cudaGetLastError());
         ++c->launches;
     }
-    auto kern = over ? db_s16x2_kernel<R, W, true> : db_s16x2_kernel<R, W, false>;
+    auto kern = over ? db_s16x2_kernel<R, W, true, G> : db_s16x2_kernel<R, W, false, G>;
     const int kp = kt_begin(c, SW_KT_DB16);
     kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
                                                          static_cast<const DevScoring *>(c->scorings.p),
@@ -86,60 +88,75 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     return SW_OK;
 }
 
-template <int R, int W>
+template <int R, int W, int G>
 int resident_blocks(sw_ctx *c, int K, int m, int *out) {
-    const size_t smem = db_profile_bytes<R>(K, m);
+    const size_t smem = db_profile_bytes<R, G>(K, m);
     if ((long long)smem > kMaxProfileSmem) return SW_ERANGE;
     static int attr_set[64] = {0};
     if (c->device < 64 && !attr_set[c->device]) {
-        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxProfileSmem));
-        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CU(cudaFuncSetAttribute(db_s16x2_kernel<R, W, true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kMaxProfileSmem));
         attr_set[c->device] = 1;
     }
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false>, W * 32, smem));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false, G>, W * 32, smem));
     if (occ < 1) return SW_ECUDA;
     *out = occ * c->nsm;
     return SW_OK;
 }
 
-// Tile shapes of the packed search: rows a lane and warps a block.  A query
-// is padded to whole passes of 32 R rows, so short queries want small R
-// (144 residues: one 160-row pass at R = 5 instead of 256 rows at R = 8);
-// long ones want R = 16, whose per-step overhead is shared by more rows.
-// Queries whose profile would not leave room for three blocks an SM take
-// blocks of 16 warps (one per SM) at R = 16.
-struct DbShape { int R, W; };
-constexpr DbShape kDbShapes[] = {{4, 8}, {5, 8}, {6, 8}, {8, 8}, {12, 8}, {16, 8}, {16, 16}};
+// Tile shapes of the packed search: rows a lane, warps a block and lanes a
+// wavefront.  A query is padded to whole passes of G R rows, so short queries
+// want few rows a pass: 144 residues take one 144-row pass in two 16-lane
+// wavefronts a warp at R = 9 (in one 32-lane wavefront: 160 rows at R = 5, with
+// a lane's fixed per-step cost shared by 5 rows instead of 9; measured 4,333
+// against 3,476 GCUPS).  Long queries want R = 16, whose per-step overhead is
+// shared by more rows.  Queries whose profile would not leave room for three
+// blocks an SM take blocks of 16 warps (one per SM) at R = 16.  (Lanes of 4, 5,
+// 6 and 12 rows in 32-lane wavefronts were measured too and never won.)
+#define SWGB_DB_SHAPES(X)                                                                              \
+    X(0, 8, 8, 32) X(1, 16, 8, 32) X(2, 4, 8, 16) X(3, 6, 8, 16) X(4, 9, 8, 16) X(5, 12, 8, 16)          \
+    X(6, 16, 16, 32)
+struct DbShape { int R, W, G; };
+#define SWGB_DB_ROW(i, R, W, G) {R, W, G},
+constexpr DbShape kDbShapes[] = {SWGB_DB_SHAPES(SWGB_DB_ROW)};
+#undef SWGB_DB_ROW
 constexpr int kDbWide = 6;                         // index of the one-block-an-SM shape
 constexpr size_t kDbNarrowProfileMax = 96 * 1024;  // profile bytes of a three-blocks-an-SM shape at most
+// cost model of a shape (db_shape), fitted to measured GCUPS of every shape at query lengths 144,
+// 300, 464, 700, 1,000 and 2,005 (it picks the fastest at each): a lane's fixed per-step cost in
+// rows' worth, a pass boundary in rows, and a typical subject length (a wavefront's skew of
+// G - 1 steps costs about (G - 1) / 360 of a pair's sweep)
+constexpr double kDbStepRows = 2.25, kDbPassRows = 16, kDbTypicalCols = 360;
 
 size_t shape_profile_bytes(int s, int K, int m) {
-    switch (kDbShapes[s].R) {
-        case 4: return db_profile_bytes<4>(K, m);
-        case 5: return db_profile_bytes<5>(K, m);
-        case 6: return db_profile_bytes<6>(K, m);
-        case 12: return db_profile_bytes<12>(K, m);
-        case 16: return db_profile_bytes<16>(K, m);
-        default: return db_profile_bytes<8>(K, m);
+    switch (s) {
+#define SWGB_DB_CASE(i, R, W, G) case i: return db_profile_bytes<R, G>(K, m);
+        SWGB_DB_SHAPES(SWGB_DB_CASE)
+#undef SWGB_DB_CASE
+        default: return 0;
     }
 }
 
 }  // namespace
 
 // The shape for a query of m residues: the least padded work, counting the
-// per-step overhead of a lane (about 1.5 rows' worth) and a pass boundary
-// (about 16 rows), among the shapes whose profile fits.
+// per-step overhead of a lane, a pass boundary and the wavefront's skew, among
+// the shapes whose profile fits.
 int swgb::db_shape(int K, int m) {
+    // tuning override: SWGB_DB_SHAPE=<index into kDbShapes>, where its profile fits
+    static const int forced = [] { const char *f = std::getenv("SWGB_DB_SHAPE"); return f ? std::atoi(f) : -1; }();
+    if (forced >= 0 && forced < kDbWide && shape_profile_bytes(forced, K, m) <= kDbNarrowProfileMax) return forced;
     int best = kDbWide;
     double best_cost = 1e300;
     for (int s = 0; s < kDbWide; ++s) {
         if (shape_profile_bytes(s, K, m) > kDbNarrowProfileMax) continue;
-        const int R = kDbShapes[s].R, rows = 32 * R;
+        const int R = kDbShapes[s].R, G = kDbShapes[s].G, rows = G * R;
         const long long passes = (m + rows - 1) / rows;
-        const double cost = (double)passes * rows * (R + 1.5) / R + 16.0 * (double)passes;
+        const double cost = (double)passes * rows * (R + kDbStepRows) / R * (1.0 + (G - 1) / kDbTypicalCols) +
+                            kDbPassRows * (double)passes;
         if (cost < best_cost) { best_cost = cost; best = s; }
     }
     return best;
@@ -147,13 +164,10 @@ int swgb::db_shape(int K, int m) {
 
 int swgb::db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out) {
     switch (shape) {
-        case 0: return resident_blocks<4, 8>(c, K, m, out);
-        case 1: return resident_blocks<5, 8>(c, K, m, out);
-        case 2: return resident_blocks<6, 8>(c, K, m, out);
-        case 3: return resident_blocks<8, 8>(c, K, m, out);
-        case 4: return resident_blocks<12, 8>(c, K, m, out);
-        case 5: return resident_blocks<16, 8>(c, K, m, out);
-        default: return resident_blocks<16, 16>(c, K, m, out);
+#define SWGB_DB_CASE(i, R, W, G) case i: return resident_blocks<R, W, G>(c, K, m, out);
+        SWGB_DB_SHAPES(SWGB_DB_CASE)
+#undef SWGB_DB_CASE
+        default: return SW_EINVAL;
     }
 }
 
@@ -162,20 +176,17 @@ int swgb::db_resident_blocks(sw_ctx *c, int K, int m, int *out) {
 }
 
 int swgb::db_shape_warps(int shape) { return kDbShapes[shape].W; }
-int swgb::db_shape_rows(int shape) { return 32 * kDbShapes[shape].R; }
+int swgb::db_shape_rows(int shape) { return kDbShapes[shape].G * kDbShapes[shape].R; }
 int swgb::db_warps_per_block(int K, int m) { return db_shape_warps(db_shape(K, m)); }
 int swgb::db_rows_per_pass(int K, int m) { return db_shape_rows(db_shape(K, m)); }
 
 int swgb::db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K,
                           int m) {
     switch (shape) {
-        case 0: return launch_db<4, 8>(c, jobs, njobs, nblocks, D, K, m);
-        case 1: return launch_db<5, 8>(c, jobs, njobs, nblocks, D, K, m);
-        case 2: return launch_db<6, 8>(c, jobs, njobs, nblocks, D, K, m);
-        case 3: return launch_db<8, 8>(c, jobs, njobs, nblocks, D, K, m);
-        case 4: return launch_db<12, 8>(c, jobs, njobs, nblocks, D, K, m);
-        case 5: return launch_db<16, 8>(c, jobs, njobs, nblocks, D, K, m);
-        default: return launch_db<16, 16>(c, jobs, njobs, nblocks, D, K, m);
+#define SWGB_DB_CASE(i, R, W, G) case i: return launch_db<R, W, G>(c, jobs, njobs, nblocks, D, K, m);
+        SWGB_DB_SHAPES(SWGB_DB_CASE)
+#undef SWGB_DB_CASE
+        default: return SW_EINVAL;
     }
 }
 

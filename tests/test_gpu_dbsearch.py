@@ -50,11 +50,13 @@ def test_small_database_all_scores(ctx, oracle_mod):
 
 
 def test_every_tile_shape(ctx, oracle_mod):
-    """Query lengths that pick each tile shape of the packed search (4, 5, 6,
-    8, 12 and 16 rows a lane, and 16-warp blocks for long queries), with one
-    or several passes and the last pass partly padding."""
+    """Query lengths that pick each tile shape of the packed search (two
+    16-lane wavefronts a warp at 4, 6, 9 and 12 rows a lane; one 32-lane
+    wavefront at 8 and 16 rows; 16-warp blocks for long queries), with one or
+    several passes, the last pass partly padding, and warps whose second
+    wavefront finds no pair left."""
     sc = W.protein_scoring()
-    lengths = (1, 31, 100, 128, 144, 160, 161, 190, 250, 300, 350, 384, 464, 700, 1000, 1500, 4100)
+    lengths = (1, 31, 80, 100, 128, 144, 160, 161, 190, 250, 300, 350, 384, 464, 700, 1000, 1500, 4100)
     qs = W.protein_queries(lengths, seed_offset=760)
     pdb = W.protein_db(400, queries=qs, seed_offset=770)
     subjects = [pdb.subject(s) for s in range(pdb.nseq)]
