@@ -40,7 +40,7 @@ using namespace swgb;
 
 namespace {
 
-constexpr int kMinBandDepth = 16;         // tile rows per band at least (three tiles per tile row)
+constexpr int kMinBandDepth = 16;         // tile rows per band at least
 constexpr long long kWalkMaxIters = 1LL << 26;
 
 int empty_alignment(sw_alignment *out) {
@@ -137,6 +137,11 @@ int launch_walk(sw_ctx *c, const void *const *table, int I0, int J0, int nI, int
         default: return SW_EINVAL;
     }
 }
+
+// Traceback band: the margin around the walk's diagonal, as a fraction of the tile side, and
+// the tile columns a row of the walk's table keeps along the diagonal.
+constexpr long long kBandMarginDiv = 8;
+constexpr int kBandWidth = 5;
 
 // Run records of paths up to this many bytes come back with every round's walk state.
 constexpr size_t kRunsEachRoundBytes = 256 * 1024;
@@ -443,14 +448,16 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(c->walk.ensure(sizeof(WalkState)));
     RC(c->runs.ensure((size_t)(ie + je + 2) * sizeof(int2)));
     WalkState w{ie, je, 0, 0, 0, -1, 0};
-    // a band of three tiles per tile row, deep enough for about one tile per SM, and its
-    // traceback bits within the budget
+    // the band's traceback bits within the budget (at most three tiles a row)
     const size_t tile_bytes = (size_t)(BT / tbc.R) * (size_t)BT * (size_t)tb_word_bytes(tbc.R);
-    int band = c->tb_band > 0 ? std::min(c->tb_band, 60) : std::max(kMinBandDepth, c->nsm / 3);
+    // tile rows per band: two or three tiles a row, about one tile per SM (measured at 200 kbp: a
+    // band as deep as the SM count, 228 tiles in one round, took 1.18 ms against 1.00 ms for two
+    // rounds of one tile per SM)
+    int band = c->tb_band > 0 ? std::min(c->tb_band, 800) : std::max(kMinBandDepth, c->nsm / 2);
     band = (int)std::max<long long>(1, std::min<long long>(band, (long long)(c->tb_budget / (3 * tile_bytes))));
     const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
     const int HS = tsw * 32 * tbc.R;                     // rows per traceback strip
-    const size_t table_cap = (size_t)(band + 1) * (band + 2);
+    const size_t table_cap = (size_t)(band + 1) * kBandWidth;
     // staging: the rounds' tile tables, then the walk's start (its own slot, so that no
     // synchronisation is needed before the first table is written)
     const size_t w_off = (table_cap * sizeof(void *) + 15) / 16 * 16;
@@ -489,15 +496,26 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         }
         const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
         const int It0 = (int)(R0c / BT), Jt0 = (int)(C0c / BT);       // the region's first tile row, column
-        const int I0 = std::max(It0, I - band + 1), J0 = std::max(Jt0, J - band);
-        const int nI = I - I0 + 1, nJ = J - J0 + 1;
+        const int I0 = std::max(It0, I - band + 1);
+        // the walk's table keeps kBandWidth tile columns a row along the diagonal: row ti holds
+        // columns [ti + kd, ti + kd + kBandWidth), which contain every tile chosen below
+        const int nI = I - I0 + 1, nJ = kBandWidth, kd = J - I - (kBandWidth - 2);
         std::vector<const void *> table((size_t)nI * nJ, nullptr);
         std::vector<FillTask> tasks;
         long long tickets = 0;
+        // tiles of each tile row: the columns that the diagonal through the walk's cell crosses
+        // in that row, widened by BT / kBandMarginDiv on each side (two tiles a row, a third where the
+        // diagonal runs near a tile edge); a path that drifts further ends the round early
+        const long long margin = BT / kBandMarginDiv;
         for (int d = 0; d < band && I - d >= It0; ++d) {
-            for (int dl = -1; dl <= 1; ++dl) {
-                const int ti = I - d, tj = J - d + dl;
-                if (tj < Jt0 || tj > J) continue;
+            const int ti = I - d;
+            const long long rlo = (long long)ti * BT, rhi = std::min<long long>((long long)(ti + 1) * BT, w.i) - 1;
+            const long long clo = (long long)(w.j - 1) - ((long long)(w.i - 1) - rlo) - margin;
+            const long long chi = (long long)(w.j - 1) - ((long long)(w.i - 1) - rhi) + margin;
+            const int wlo = ti + kd, whi = wlo + kBandWidth - 1;             // the table's window
+            const int tlo = (int)std::min<long long>(J, std::max<long long>(std::max(Jt0, wlo), clo < 0 ? 0 : clo / BT));
+            const int thi = (int)std::min<long long>(std::min(J, whi), std::max<long long>(tlo, chi < 0 ? 0 : chi / BT));
+            for (int tj = tlo; tj <= thi; ++tj) {
                 FillTask u{};
                 const long long r0 = (long long)ti * BT, c0 = (long long)tj * BT;
                 u.a = da + r0;
@@ -534,7 +552,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.tb_ld = BT;
                 tickets += u.nstrips;
                 tasks.push_back(u);
-                table[(size_t)(ti - I0) * nJ + (tj - J0)] = u.tb;
+                table[(size_t)(ti - I0) * nJ + (tj - (kd + I0) - (ti - I0))] = u.tb;
             }
         }
         RC(run_fill(c, tbc, kModeTb, fold, tasks, tickets, ds.K));
@@ -542,7 +560,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         if (tbytes > c->stage2.cap) return SW_EINVAL;
         std::memcpy(c->stage2.p, table.data(), tbytes);
         CU(cudaMemcpyAsync(c->misc.p, c->stage2.p, tbytes, cudaMemcpyHostToDevice, c->stream));
-        RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), I0, J0, nI, nJ, (int)BT, R));
+        RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), I0, kd + I0, nI, nJ, (int)BT, R));
         CU(cudaMemcpyAsync(c->stage3.p, c->walk.p, sizeof(WalkState), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 64, c->err.p, sizeof(int),
                            cudaMemcpyDeviceToHost, c->stream));

@@ -42,9 +42,10 @@ struct WalkState {
     int32_t cur_len;
 };
 
-// The tiles recomputed in one round: a dense table over tile rows
-// [I0, I0 + nI) and tile columns [J0, J0 + nJ); a null entry means the tile
-// was not computed.  Words of a tile: [local row / R][local column], ld = BT.
+// The tiles recomputed in one round: for each tile row I in [I0, I0 + nI), a
+// window of nJ tile columns that follows the diagonal, [J0 + (I - I0),
+// J0 + (I - I0) + nJ); a null entry means the tile was not computed.  Words of
+// a tile: [local row / R][local column], ld = BT.
 template <typename Word>
 struct TileTable {
     const Word *const *bits;   // nI * nJ entries
@@ -85,7 +86,7 @@ struct WalkWindow {
 
 template <typename Word>
 __device__ __forceinline__ const Word *tile_ptr(const TileTable<Word> &T, const Word *const *tiles, int I, int J) {
-    const int ti = I - T.I0, tj = J - T.J0;
+    const int ti = I - T.I0, tj = J - (T.J0 + ti);
     return (ti >= 0 && tj >= 0 && ti < T.nI && tj < T.nJ) ? tiles[ti * T.nJ + tj] : nullptr;
 }
 
