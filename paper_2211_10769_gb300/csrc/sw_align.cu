@@ -152,9 +152,11 @@ constexpr long long kMaxOneLevelBT = 16384;
 // Two levels of checkpoints: fill the part of coarse tile (CI, CJ) above and left
 // of (Wi0, Wj0) again, entered from the forward fill's checkpoint row above it and
 // its staircase column left of it, keeping checkpoint rows and staircase columns
-// every BT2 inside it: the int32 fill with the forward fill's rows per lane (so
-// that it can enter that fill's staircase column, in either form).  Memory for
-// the refill's checkpoints is about 16 BT1^2 / BT2 bytes, for any pair size.
+// every BT2 inside it: the forward fill's own kind (the packed fill enters its
+// two-positions staircase as its state after step -1; the int32 fill its
+// staircase through the prologue) with its rows per lane, so that the refill's
+// staircase columns have the forward fill's form too.  Memory for the refill's
+// checkpoints is about 16 BT1^2 / BT2 bytes, for any pair size.
 int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t n, const DevScoring &ds,
                        const FillConfig &fwd, bool fold, int aux_rows, const int2 *rowck, const int2 *colck,
                        const int2 *colaux, long long colck_ld, long long colaux_ld, long long CI, long long CJ,
@@ -162,6 +164,7 @@ int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t 
                        const int2 **rowck2, const int2 **colck2, const int2 **colaux2, long long *ld2, long long *N2) {
     FillConfig fc{fwd.R, 4};
     fc.alg = fwd.alg;
+    fc.P16 = fwd.P16;
     const int HC2 = 4 * 32 * fc.R;
     const long long M2 = Wi0 - R0c, W2 = Wj0 - C0c;
     FillTask t{};
@@ -187,11 +190,12 @@ int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t 
     t.colck_every = (int32_t)BT2;
     t.colck_ld = (long long)t.nstrips * HC2;
     RC(c->colck2.ensure((size_t)nc * (size_t)t.colck_ld * sizeof(int2)));
-    RC(c->colaux2.ensure((size_t)nc * (size_t)(t.colck_ld / fc.R) * sizeof(int2)));
+    RC(c->colaux2.ensure((size_t)nc * (size_t)(t.colck_ld / aux_rows) * sizeof(int2)));
     // the fill writes column checkpoints at colck + k ld + (row0 + row) and their row-group
-    // records at colck_aux + k ld / R + (row0 + row) / R: based so that row0 lands on 0
+    // records at colck_aux + k ld / A + (row0 + row) / A (A = rows a record: R, or R / 2 for the
+    // packed fill's half-groups): based so that row0 lands on 0
     t.colck = static_cast<int2 *>(c->colck2.p) - R0c;
-    t.colck_aux = static_cast<int2 *>(c->colaux2.p) - R0c / fc.R;
+    t.colck_aux = static_cast<int2 *>(c->colaux2.p) - R0c / aux_rows;
     RC(run_fill(c, fc, kModeScoreCk, fold, {t}, t.nstrips, ds.K));
     int e = 0;
     RC(read_err(c, &e));          // synchronises: the next fill reuses the staging buffer
@@ -539,8 +543,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                     u.left_split = fwd.P16 ? 1 : 0;
                 } else {
                     u.left = colck2 + (size_t)((c0 - C0c) / BT - 1) * ld2 + (r0 - R0c);
-                    u.left_aux = colaux2 + (size_t)((c0 - C0c) / BT - 1) * (ld2 / R) + (r0 - R0c) / R;
-                    u.left_split = 0;
+                    u.left_aux = colaux2 + (size_t)((c0 - C0c) / BT - 1) * (ld2 / aux_rows) + (r0 - R0c) / aux_rows;
+                    u.left_split = fwd.P16 ? 1 : 0;
                 }
                 const size_t k = tasks.size();
                 u.nslot = std::min(u.nstrips, 2);

@@ -448,7 +448,8 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
                 const int c = min((int)T.b[col], K);
                 bring[col & (QB - 1)] = (uint8_t)c;
                 // pair profile (packed fill): the byte offset of the entry for (b[col], b[col - 1])
-                if (poff) poff[col & (QB - 1)] = (c * pk1 + (col > 0 ? min((int)T.b[col - 1], K) : K)) * pstride;
+                if (poff)   // (column -1 is real for a task entered from a checkpoint column)
+                    poff[col & (QB - 1)] = (c * pk1 + ((col > 0 || T.left) ? min((int)T.b[col - 1], K) : K)) * pstride;
             }
             __syncwarp();
             if (lane == 0) sts_release(&prod[0], target);

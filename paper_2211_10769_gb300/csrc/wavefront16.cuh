@@ -237,6 +237,50 @@ __device__ __forceinline__ void p16_step(P16Lane<R> &st, const uint32_t (&pw)[R 
     st.bcol[1] = ph ? st.bcol[1] : j - 1;
 }
 
+// A task that starts right of a checkpoint column written by this fill (the
+// two-positions staircase of the checkpoint mode, FillTask::left_split):
+// lane l's top half holds its rows at column -1 - 2l and its bottom half at
+// -2 - 2l (task columns), which is exactly the wavefront's state after step
+// -1.  The lane takes that state (scaled by 8, in a base of its own) and the
+// sweep goes on from step 0; its first steps recompute real columns left of
+// the task from real residues (the residue ring's slots left of column 0).
+template <int R>
+__device__ __forceinline__ void p16_enter_staircase(const FillTask &T, P16Lane<R> &st, int grow, int lane, int go,
+                                                    int ge) {
+    constexpr int H = R / 2;
+    int vU[R], vE[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int2 v = make_int2(-go, kNeg);
+        if (grow + r < T.rows) v = __ldcg(T.left + grow + r);
+        vU[r] = v.x;
+        vE[r] = v.y;
+    }
+    const bool in = grow < T.rows;
+    const int2 at = in ? __ldcg(T.left_aux + grow / H) : make_int2(-go, kNeg);       // top half
+    const int2 ab = in ? __ldcg(T.left_aux + grow / H + 1) : make_int2(-go, kNeg);   // bottom half
+    // absolute values scaled by 8 (-infinity clamped first so that scaling cannot overflow), then
+    // relative to the lane's base, -infinity at kNeg16p
+    auto scaled = [](int v) { return max(v, -(1 << 20)) * 8; };
+    const int B = max(0, scaled(vU[0]) - kP16Center) & ~7;
+    auto rel = [&](int v) { return max(scaled(v) - B, kNeg16p); };
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        st.U[k] = p16_pack(rel(vU[k]), rel(vU[H + k]));
+        st.E[k] = p16_pack(rel(vE[k]), rel(vE[H + k]));
+    }
+    st.udiag0 = p16_pack(rel(at.x), rel(ab.x));
+    st.flast = p16_pack(rel(at.y), rel(ab.y));
+    st.ub = st.U[H - 1];
+    // F of the row below each half's last row: max(F - extend, H - open) of that row
+    st.fb = __viaddmax_s16x2(st.flast, p16_pack(-8 * ge, -8 * ge), st.U[H - 1]);
+    st.B = B;
+    const int bup = __shfl_up_sync(kFull, B, 1);
+    st.din2 = lane == 0 ? 0u : p16_pack(bup - B, 0);
+    // the best keys in the new base (H = 0 with the largest tag, never a best), kept above -32768
+    st.kbest = p16_pack(max(st.best[0] - B, -32768), max(st.best[1] - B, -32768));
+}
+
 // Lane 0's row above at one step, from the strip's boundary row v (scaled,
 // absolute: H - open and F): both taken to lane 0's base B0 and into the high
 // halves, the F as the first row's F, max(F - extend, H - open).
@@ -328,14 +372,21 @@ wavefront16_kernel(const FillLaunch L)
                 p16[idx] = (int16_t)(ok ? 8 * (SC.mat[min((int)T.a[rbase + lr], K - 1) * K + c] + go) : 8 * kPadScore);
             }
         }
-        // the residue ring's last kP16Pos slots read as padding: lanes compute the columns left
-        // of the task (down to -63) during their first two chunks; the input warp reaches those
-        // slots only after the last warp has published a column, i.e. left those chunks
+        // the residue ring's last kP16Pos slots hold the columns left of the task (down to -64),
+        // which lanes compute during their first two chunks: padding at the matrix border;
+        // the input warp reaches those slots only after the last warp has published a column,
+        // i.e. left those chunks
         // bytes per profile entry: pair, per residue combination; int16, per residue
         const int pstride = PK == kP16Pair ? (R / 4) * NL * 8 : 2 * HC;
+        // (a task entered from a checkpoint column: the real residues of those columns)
         if (threadIdx.x < kP16Pos) {
-            bring[QB - kP16Pos + threadIdx.x] = (uint8_t)K;
-            if constexpr (PK == kP16Pair) s_poff[QB - kP16Pos + threadIdx.x] = (K * (K + 1) + K) * pstride;
+            const int j = (int)threadIdx.x - kP16Pos;                       // column -64 .. -1
+            const int cj = T.left ? min((int)T.b[j], K) : K;
+            bring[QB - kP16Pos + threadIdx.x] = (uint8_t)cj;
+            if constexpr (PK == kP16Pair) {
+                const int cjm = T.left ? min((int)T.b[j - 1], K) : K;
+                s_poff[QB - kP16Pos + threadIdx.x] = (cj * (K + 1) + cjm) * pstride;
+            }
         }
         __syncthreads();
 
@@ -364,14 +415,21 @@ wavefront16_kernel(const FillLaunch L)
             st.best[0] = st.best[1] = -8 * go + 7;
             st.bcol[0] = st.bcol[1] = -1;
             st.kbest = p16_pack(st.best[0], st.best[1]);
+            if (T.left) p16_enter_staircase<R>(T, st, grow, lane, go, ge);   // (a two-positions staircase)
             int next_ck = (MODE == kModeScoreCk && T.colck && T.colck_every > 0) ? T.colck_every - 1 : 0x7fffffff;
             int2 *rin = ring[warp];
             int2 *rout = ring[warp + 1];
             int seen_in = 0;
             bool loaded = false;
             uint32_t pw[R / 2], pwp[R / 2];
+            if constexpr (PK == kP16Pair) {
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);
+                for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);   // (unused)
+            } else {
+                // the int16 profile's bottom half takes the previous step's words: at step 0 those
+                // of column -1 - 2 lane (padding, or a real residue left of a checkpoint column)
+                p16_load<R, PK, NL>(prow + min((int)bring[(-1 - 2 * lane) & (QB - 1)], K) * pstride, pwp);
+            }
             uint2 top;
             for (int s0 = 0; s0 < n + LAG; s0 += CH) {
                 const int need_in = min(n, s0 + CH + 1);
@@ -383,17 +441,20 @@ wavefront16_kernel(const FillLaunch L)
                 const int out_hi = min(n, ring_hi);
                 if (ring_hi > 0 && !warp_wait_geq(&cons[warp + 1], ring_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
                 if (!loaded) {
-                    const int c = min((int)bring[(s0 - 2 * lane) & (QB - 1)], K);
-                    // (the sweep's first step: the bottom halves' column is left of the task, padding)
-                    if constexpr (PK == kP16Pair) p16_load<R, PK, NL>(prow + (c * (K + 1) + K) * pstride, pw);
-                    else p16_load<R, PK, NL>(prow + c * pstride, pw);
+                    if constexpr (PK == kP16Pair) {
+                        p16_load<R, PK, NL>(prow + s_poff[(s0 - 2 * lane) & (QB - 1)], pw);
+                    } else {
+                        const int c = min((int)bring[(s0 - 2 * lane) & (QB - 1)], K);
+                        p16_load<R, PK, NL>(prow + c * pstride, pw);
+                    }
                     loaded = true;
                 }
                 {   // new lane base from the top half's first row at its last column; the best
                     // keys go through their absolute copies
                     const int oldB = st.B;
-                    st.best[0] = max(st.best[0], p16_lo(st.kbest) + oldB);
-                    st.best[1] = max(st.best[1], p16_hi(st.kbest) + oldB);
+                    // (-32768: no key since a staircase entry put the best below the base)
+                    if (p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + oldB);
+                    if (p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + oldB);
                     const int ref = p16_lo(st.U[0]) + oldB;
                     const int Bn = max(0, ref - kP16Center) & ~7;
                     const unsigned d2 = p16_pack(oldB - Bn, oldB - Bn);
@@ -409,7 +470,7 @@ wavefront16_kernel(const FillLaunch L)
                     st.B = Bn;
                     const int bup = __shfl_up_sync(kFull, Bn, 1);
                     st.din2 = lane == 0 ? 0u : p16_pack(bup - Bn, 0);
-                    st.kbest = p16_pack(min(st.best[0] - Bn, 32767), min(st.best[1] - Bn, 32767));
+                    st.kbest = p16_pack(max(min(st.best[0] - Bn, 32767), -32768), max(min(st.best[1] - Bn, 32767), -32768));
                 }
                 {   // lane 0's rows above for the chunk's steps, taken to its new base once per
                     // chunk (one entry a lane) rather than once per step; entries at or past n
@@ -498,8 +559,8 @@ wavefront16_kernel(const FillLaunch L)
                     if (out_hi > 0) sts_release(&prod[warp + 1], out_hi);
                 }
             }
-            st.best[0] = max(st.best[0], p16_lo(st.kbest) + st.B);
-            st.best[1] = max(st.best[1], p16_hi(st.kbest) + st.B);
+            if (p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + st.B);
+            if (p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + st.B);
 
             // the lane's candidate: the better of its halves (top rows come first)
             int cs = 0, cj = 0x7fffffff, ci = 0x7fffffff;

@@ -65,6 +65,25 @@ def test_every_tile_shape(ctx, oracle_mod):
         _check_all(ctx, oracle_mod, db, subjects, q, sc)
 
 
+@pytest.mark.parametrize("nseq", [1, 2, 3, 5, 7])
+def test_tiny_databases_short_queries(ctx, oracle_mod, nseq):
+    """One to four subject pairs against queries that take the two-wavefront
+    shapes: most warps find one pair or none, and a warp's second wavefront
+    often has no pair (its lanes still take part in the shuffles)."""
+    sc = W.protein_scoring()
+    g = np.random.default_rng(W.BASE_SEED + 780 + nseq)
+    subjects = [W.random_protein(int(g.integers(1, 400)), W.BASE_SEED + 790 + 10 * nseq + i) for i in range(nseq)]
+    db = _db(ctx, subjects)
+    for m in (5, 60, 90, 140, 190):
+        q = W.random_protein(m, W.BASE_SEED + 800 + m)
+        if nseq > 2:
+            subjects_q = list(subjects)
+            subjects_q[1] = W.mutate(q, 20, W.BASE_SEED + 801 + m, p_sub=0.2)   # a homolog among them
+            dbq = _db(ctx, subjects_q)
+            _check_all(ctx, oracle_mod, dbq, subjects_q, q, sc, k=min(4, nseq))
+        _check_all(ctx, oracle_mod, db, subjects, q, sc, k=min(4, nseq))
+
+
 def test_long_query_and_dna(ctx, oracle_mod):
     sc = W.protein_scoring()
     q = W.protein_queries((5478,))[0]

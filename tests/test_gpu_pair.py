@@ -338,11 +338,13 @@ def test_align_one_round_limit(ctx, oracle_mod, side):
 
 
 @pytest.mark.parametrize("sides,env", [("3072,1024", {}), ("3072,1024", {"SWGB_P16": "0"}),
+                                       ("3072,1024", {"SWGB_FWD": "8,4,0,2,1"}),
                                        ("4608,1536", {"SWGB_FWD": "12,4,0,2,1"}), ("2048,1024", {})])
 def test_two_level_checkpoints(oracle_mod, monkeypatch, sides, env):
     """Two levels of checkpoints (forced small sides): the forward fill keeps
     every BT1-th row and column, each coarse tile the path enters is filled
-    again from them with checkpoints every BT2, and the traceback tiles start
+    again from them with checkpoints every BT2 (by the packed fill entering its
+    own checkpoint column, or the int32 fill), and the traceback tiles start
     from either level.  Paths with long gaps cross coarse tiles in both
     directions; DNA (packed and int32 forward fills) and protein."""
     from paper_2211_10769_gb300 import binding
