@@ -203,9 +203,7 @@ __device__ __forceinline__ bool warp_wait_geq(const int *ctr, int want, const vo
     while (lds_acquire(ctr) < want) {
         if (*abort_flag) return false;
         if (++it > limit) { atomicCAS(err, 0, kErrTimeout); return false; }
-#ifndef SWGB_WAIT_SPIN
         if (it > 64) __nanosleep(20);              // spin first: the producer is usually a step away
-#endif
     }
     return true;
 }
@@ -464,15 +462,8 @@ __device__ __forceinline__ void fill_input_warp(const FillTask &T, const FillLau
             }
             // far ahead of warp 0 (more than two batches buffered): poll rarely, so that the
             // compute warp sharing this SM sub-partition keeps its issue slots
-#ifndef SWGB_INPUT_EAGER
             if (in_next - lds_acquire(&cons[0]) > 2 * IOB) __nanosleep(256);
-            else
-#endif
-#ifndef SWGB_IO_SPIN
-            if (idle > 32) __nanosleep(32);
-#else
-            { }
-#endif
+            else if (idle > 32) __nanosleep(32);
         }
     }
 }
@@ -523,9 +514,7 @@ __device__ __forceinline__ void fill_output_warp(const FillTask &T, const FillLa
                 *s_abort = 1;
                 break;
             }
-#ifndef SWGB_IO_SPIN
             if (idle > 32) __nanosleep(32);
-#endif
         }
     }
 }

@@ -67,11 +67,7 @@ constexpr int kP16Span = 16000;     // largest scaled value spread (p16_spread) 
 constexpr int kP16QS = 512;         // boundary-ring columns per channel
 constexpr int kP16Pos = 64;         // wavefront positions per warp (two per lane)
 constexpr int kP16Shift = 3;        // values are multiplied by 2^3
-#ifndef SWGB_P16_CH
-constexpr int kP16CH = 32;          // steps per chunk (hand-off, base change)
-#else
-constexpr int kP16CH = SWGB_P16_CH;
-#endif
+constexpr int kP16CH = 32;          // steps per chunk (hand-off, base change; 16 measured slower)
 
 // Profile kinds of the packed fill.
 enum P16Prof { kP16Pair = 0, kP16Int16 = 1 };
@@ -293,11 +289,7 @@ __device__ __forceinline__ uint2 p16_top_row(int2 v, int B0, int ge8) {
 // Steps per unrolled body of the steady loop, measured on GB300 (2, 4, 8, 16, 32 at 12 rows a lane): 8 for
 // the score fill; 16 with checkpoints above 8 rows a lane (its chunk-end code runs once per 16 steps); 32
 // is much slower (a body that large no longer stays in the instruction cache).
-#ifndef SWGB_P16_UNROLL
 constexpr int fill16_unroll(int R, int MODE) { return (R <= 8 || MODE == kModeScore) ? 8 : 16; }
-#else
-constexpr int fill16_unroll(int, int) { return SWGB_P16_UNROLL; }
-#endif
 
 template <int R, int W, int MODE, int PK>
 __global__ void __launch_bounds__((W + 2) * 32, 1)
