@@ -226,9 +226,9 @@ def serve(ctx, torch, stream, args):
                     "offered_gcups": round(rate * cells / len(reqs) / 1e9, 1)})
         # the device's capacity is its busy-time throughput: above it the queue grows
         out[-1]["load"] = "overload" if out[-1]["offered_gcups"] > out[-1]["busy_gcups"] else "below capacity"
-    # the same kind of requests searched one at a time with sw_dbsearch (a seeded sample of 100):
-    # the serial rate the server's continuous batching is compared with
-    sample = [q for _, q in W.serving_requests(100, 2000.0)]
+    # the requests of the highest rate searched one at a time with sw_dbsearch: the serial rate
+    # the server's continuous batching is compared with, on the same queries
+    sample = [q for _, q in W.serving_requests(args.serve_requests, max(rates))]
     db.search(sample[0], sc.matrix, sc.gap_open, sc.gap_extend, k=20)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -239,7 +239,7 @@ def serve(ctx, torch, stream, args):
     db.close()
     return {"workload": "serving_poisson_protein_vs_500k", "chunks": 8, "max_slots": 64, "k": 20,
             "serial_dbsearch_gcups": serial_gcups,
-            "serial_note": "100 requests of the same length distribution, one sw_dbsearch call each, wall clock",
+            "serial_note": "the highest rate's requests, one sw_dbsearch call each, wall clock",
             "note": "load = offered GCUPS (rate x mean cells per request) against the busy-time GCUPS; under "
                     "overload latency is queue-dominated",
             "rates": out}
