@@ -15,9 +15,9 @@ namespace {
 // largest pair profile (small alphabets); larger alphabets take the int16 profile
 constexpr size_t kPairProfileMax = 110 * 1024;
 
-template <int R, int W, int MODE, int PK>
+template <int R, int W, int MODE, int PK, bool LEFT>
 int launch16(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int max_blocks) {
-    auto kern = wavefront16_kernel<R, W, MODE, PK>;
+    auto kern = wavefront16_kernel<R, W, MODE, PK, LEFT>;
     const size_t smem = p16_profile_bytes(R, W, K, PK);
     static int attr_set[64] = {0};
     if (c->device >= 64 || !attr_set[c->device]) {
@@ -38,15 +38,18 @@ int launch16(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int max_b
     return SW_OK;
 }
 
-template <int R, int MODE>
+template <int R, int MODE, bool LEFT = false>
 int launch16_pk(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int B) {
     if (p16_profile_bytes(R, 4, K, kP16Pair) <= kPairProfileMax)
-        return launch16<R, 4, MODE, kP16Pair>(c, L, K, tickets, B);
-    return launch16<R, 4, MODE, kP16Int16>(c, L, K, tickets, B);
+        return launch16<R, 4, MODE, kP16Pair, LEFT>(c, L, K, tickets, B);
+    return launch16<R, 4, MODE, kP16Int16, LEFT>(c, L, K, tickets, B);
 }
 
+// left: the coarse-tile refills (checkpoint mode only), whose tasks enter the
+// fill at a checkpoint column.
 template <int R>
-int launch16_mode(sw_ctx *c, int mode, const FillLaunch &L, int K, long long tickets, int B) {
+int launch16_mode(sw_ctx *c, int mode, bool left, const FillLaunch &L, int K, long long tickets, int B) {
+    if (left) return mode == kModeScoreCk ? launch16_pk<R, kModeScoreCk, true>(c, L, K, tickets, B) : SW_EINVAL;
     switch (mode) {
         case kModeScore: return launch16_pk<R, kModeScore>(c, L, K, tickets, B);
         case kModeScoreCk: return launch16_pk<R, kModeScoreCk>(c, L, K, tickets, B);
@@ -69,9 +72,9 @@ int swgb::launch_fill16(sw_ctx *c, const FillConfig &cfg, int mode, const FillLa
     if (tickets <= 0) return SW_OK;
     if (cfg.W != 4) return SW_EINVAL;
     switch (cfg.R) {
-        case 8: return launch16_mode<8>(c, mode, L, K, tickets, cfg.B);
-        case 12: return launch16_mode<12>(c, mode, L, K, tickets, cfg.B);
-        case 16: return launch16_mode<16>(c, mode, L, K, tickets, cfg.B);
+        case 8: return launch16_mode<8>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
+        case 12: return launch16_mode<12>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
+        case 16: return launch16_mode<16>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
         default: return SW_EINVAL;
     }
 }

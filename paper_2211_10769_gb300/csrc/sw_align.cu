@@ -165,6 +165,7 @@ int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t 
     FillConfig fc{fwd.R, 4};
     fc.alg = fwd.alg;
     fc.P16 = fwd.P16;
+    fc.left = 1;
     const int HC2 = 4 * 32 * fc.R;
     const long long M2 = Wi0 - R0c, W2 = Wj0 - C0c;
     FillTask t{};
@@ -513,6 +514,8 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         const long long margin = BT / kBandMarginDiv;
         for (int d = 0; d < band && I - d >= It0; ++d) {
             const int ti = I - d;
+            // one tile per SM at most (a second wave would double the round's time); whole rows
+            if (d > 0 && (int)tasks.size() + kBandWidth - 2 > c->nsm) break;
             const long long rlo = (long long)ti * BT, rhi = std::min<long long>((long long)(ti + 1) * BT, w.i) - 1;
             const long long clo = (long long)(w.j - 1) - ((long long)(w.i - 1) - rlo) - margin;
             const long long chi = (long long)(w.j - 1) - ((long long)(w.i - 1) - rhi) + margin;

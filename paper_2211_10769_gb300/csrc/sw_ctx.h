@@ -46,6 +46,7 @@ struct FillConfig {
     int B = 0;
     int P16 = 0;   // packed 16-bit fill (wavefront16.cuh) instead of the int32 one
     int alg = 0;   // not kAlgLocal: the int32 fill without the zero floor (fill_variants.cu)
+    int left = 0;  // packed fill whose tasks may start right of its own checkpoint column
 };
 
 // Device time per kernel kind (sw_ctx_timing): event pairs recorded around

@@ -291,7 +291,10 @@ __device__ __forceinline__ uint2 p16_top_row(int2 v, int B0, int ge8) {
 // is much slower (a body that large no longer stays in the instruction cache).
 constexpr int fill16_unroll(int R, int MODE) { return (R <= 8 || MODE == kModeScore) ? 8 : 16; }
 
-template <int R, int W, int MODE, int PK>
+// LEFT: the tasks may start right of a checkpoint column written by this fill
+// (p16_enter_staircase; the coarse-tile refills of a two-level reconstruction).
+// A separate instantiation, so that the others compile exactly without it.
+template <int R, int W, int MODE, int PK, bool LEFT = false>
 __global__ void __launch_bounds__((W + 2) * 32, 1)
 wavefront16_kernel(const FillLaunch L)
 {
@@ -373,10 +376,11 @@ wavefront16_kernel(const FillLaunch L)
         // (a task entered from a checkpoint column: the real residues of those columns)
         if (threadIdx.x < kP16Pos) {
             const int j = (int)threadIdx.x - kP16Pos;                       // column -64 .. -1
-            const int cj = T.left ? min((int)T.b[j], K) : K;
+            const bool real = LEFT && T.left;
+            const int cj = real ? min((int)T.b[j], K) : K;
             bring[QB - kP16Pos + threadIdx.x] = (uint8_t)cj;
             if constexpr (PK == kP16Pair) {
-                const int cjm = T.left ? min((int)T.b[j - 1], K) : K;
+                const int cjm = real ? min((int)T.b[j - 1], K) : K;
                 s_poff[QB - kP16Pos + threadIdx.x] = (cj * (K + 1) + cjm) * pstride;
             }
         }
@@ -407,16 +411,17 @@ wavefront16_kernel(const FillLaunch L)
             st.best[0] = st.best[1] = -8 * go + 7;
             st.bcol[0] = st.bcol[1] = -1;
             st.kbest = p16_pack(st.best[0], st.best[1]);
-            if (T.left) p16_enter_staircase<R>(T, st, grow, lane, go, ge);   // (a two-positions staircase)
+            if constexpr (LEFT)
+                if (T.left) p16_enter_staircase<R>(T, st, grow, lane, go, ge);   // (a two-positions staircase)
             int next_ck = (MODE == kModeScoreCk && T.colck && T.colck_every > 0) ? T.colck_every - 1 : 0x7fffffff;
             int2 *rin = ring[warp];
             int2 *rout = ring[warp + 1];
             int seen_in = 0;
             bool loaded = false;
             uint32_t pw[R / 2], pwp[R / 2];
-            if constexpr (PK == kP16Pair) {
+            if constexpr (PK == kP16Pair || !LEFT) {
 #pragma unroll
-                for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);   // (unused)
+                for (int q = 0; q < R / 2; ++q) pwp[q] = p16_pack(8 * kPadScore, 8 * kPadScore);
             } else {
                 // the int16 profile's bottom half takes the previous step's words: at step 0 those
                 // of column -1 - 2 lane (padding, or a real residue left of a checkpoint column)
@@ -433,10 +438,12 @@ wavefront16_kernel(const FillLaunch L)
                 const int out_hi = min(n, ring_hi);
                 if (ring_hi > 0 && !warp_wait_geq(&cons[warp + 1], ring_hi - QS, &s_abort, L.spin_limit, L.err)) { s_abort = 1; break; }
                 if (!loaded) {
+                    const int c = min((int)bring[(s0 - 2 * lane) & (QB - 1)], K);
                     if constexpr (PK == kP16Pair) {
-                        p16_load<R, PK, NL>(prow + s_poff[(s0 - 2 * lane) & (QB - 1)], pw);
+                        // the bottom halves' column is left of the task: padding, or (LEFT) a real residue
+                        if constexpr (LEFT) p16_load<R, PK, NL>(prow + s_poff[(s0 - 2 * lane) & (QB - 1)], pw);
+                        else p16_load<R, PK, NL>(prow + (c * (K + 1) + K) * pstride, pw);
                     } else {
-                        const int c = min((int)bring[(s0 - 2 * lane) & (QB - 1)], K);
                         p16_load<R, PK, NL>(prow + c * pstride, pw);
                     }
                     loaded = true;
@@ -444,9 +451,13 @@ wavefront16_kernel(const FillLaunch L)
                 {   // new lane base from the top half's first row at its last column; the best
                     // keys go through their absolute copies
                     const int oldB = st.B;
-                    // (-32768: no key since a staircase entry put the best below the base)
-                    if (p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + oldB);
-                    if (p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + oldB);
+                    if constexpr (LEFT) {   // (-32768: no key since the staircase entry put the best below the base)
+                        if (p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + oldB);
+                        if (p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + oldB);
+                    } else {
+                        st.best[0] = max(st.best[0], p16_lo(st.kbest) + oldB);
+                        st.best[1] = max(st.best[1], p16_hi(st.kbest) + oldB);
+                    }
                     const int ref = p16_lo(st.U[0]) + oldB;
                     const int Bn = max(0, ref - kP16Center) & ~7;
                     const unsigned d2 = p16_pack(oldB - Bn, oldB - Bn);
@@ -462,7 +473,10 @@ wavefront16_kernel(const FillLaunch L)
                     st.B = Bn;
                     const int bup = __shfl_up_sync(kFull, Bn, 1);
                     st.din2 = lane == 0 ? 0u : p16_pack(bup - Bn, 0);
-                    st.kbest = p16_pack(max(min(st.best[0] - Bn, 32767), -32768), max(min(st.best[1] - Bn, 32767), -32768));
+                    if constexpr (LEFT)
+                        st.kbest = p16_pack(max(min(st.best[0] - Bn, 32767), -32768), max(min(st.best[1] - Bn, 32767), -32768));
+                    else
+                        st.kbest = p16_pack(min(st.best[0] - Bn, 32767), min(st.best[1] - Bn, 32767));
                 }
                 {   // lane 0's rows above for the chunk's steps, taken to its new base once per
                     // chunk (one entry a lane) rather than once per step; entries at or past n
@@ -551,8 +565,8 @@ wavefront16_kernel(const FillLaunch L)
                     if (out_hi > 0) sts_release(&prod[warp + 1], out_hi);
                 }
             }
-            if (p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + st.B);
-            if (p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + st.B);
+            if (!LEFT || p16_lo(st.kbest) > -32768) st.best[0] = max(st.best[0], p16_lo(st.kbest) + st.B);
+            if (!LEFT || p16_hi(st.kbest) > -32768) st.best[1] = max(st.best[1], p16_hi(st.kbest) + st.B);
 
             // the lane's candidate: the better of its halves (top rows come first)
             int cs = 0, cj = 0x7fffffff, ci = 0x7fffffff;
