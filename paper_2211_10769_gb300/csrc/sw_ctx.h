@@ -134,7 +134,10 @@ int db_shape(int K, int m);                // tile shape (index) for a query of 
 int db_shape_warps(int shape);
 int db_shape_rows(int shape);              // query rows per pass
 int db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out);
-int db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m);
+// rows / slots: the launch's boundary-row scratch and slot pool (default: the context's; launches that
+// run concurrently on different streams need their own)
+int db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m,
+                    DevBuf *rows = nullptr, DevBuf *slots = nullptr);
 int db_resident_blocks(sw_ctx *c, int K, int m, int *out);
 int db_warps_per_block(int K, int m);
 int db_rows_per_pass(int K, int m);      // query rows per pass of the packed kernel for this launch shape

@@ -52,7 +52,8 @@ size_t db_profile_bytes(int K, int m) {
 }
 
 template <int R, int W, int G>
-int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m) {
+int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m, DevBuf &rows,
+              DevBuf &slots) {
     const size_t smem = db_profile_bytes<R, G>(K, m);
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false, G>, W * 32, smem));
@@ -67,9 +68,9 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     D.slot_words = (D.nslots + 31) / 32;
     const bool over = nblocks > D.nslots;
     // (one boundary row per wavefront: 32 / G of them a warp)
-    RC(c->dbscratch.ensure((size_t)D.nslots * W * (32 / G) * (size_t)(D.maxlen + 1) * sizeof(uint2)));
-    RC(c->dbslots.ensure((size_t)D.slot_words * sizeof(unsigned)));
-    D.slot_pool = static_cast<unsigned *>(c->dbslots.p);
+    RC(rows.ensure((size_t)D.nslots * W * (32 / G) * (size_t)(D.maxlen + 1) * sizeof(uint2)));
+    RC(slots.ensure((size_t)D.slot_words * sizeof(unsigned)));
+    D.slot_pool = static_cast<unsigned *>(slots.p);
     D.err = static_cast<int *>(c->err.p);
     D.spin_limit = c->spin_limit;
     if (over) {
@@ -81,7 +82,7 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     const int kp = kt_begin(c, SW_KT_DB16);
     kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
                                                          static_cast<const DevScoring *>(c->scorings.p),
-                                                         static_cast<uint2 *>(c->dbscratch.p));
+                                                         static_cast<uint2 *>(rows.p));
     kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
@@ -181,9 +182,11 @@ int swgb::db_warps_per_block(int K, int m) { return db_shape_warps(db_shape(K, m
 int swgb::db_rows_per_pass(int K, int m) { return db_shape_rows(db_shape(K, m)); }
 
 int swgb::db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K,
-                          int m) {
+                          int m, DevBuf *rows, DevBuf *slots) {
+    DevBuf &r = rows ? *rows : c->dbscratch;
+    DevBuf &s = slots ? *slots : c->dbslots;
     switch (shape) {
-#define SWGB_DB_CASE(i, R, W, G) case i: return launch_db<R, W, G>(c, jobs, njobs, nblocks, D, K, m);
+#define SWGB_DB_CASE(i, R, W, G) case i: return launch_db<R, W, G>(c, jobs, njobs, nblocks, D, K, m, r, s);
         SWGB_DB_SHAPES(SWGB_DB_CASE)
 #undef SWGB_DB_CASE
         default: return SW_EINVAL;

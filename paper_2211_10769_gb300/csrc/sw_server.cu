@@ -68,6 +68,16 @@ struct sw_server {
     int maxK = 0;
     long long cells_done = 0;       // cells of retired requests
     int64_t total_res = 0;
+    // one stream per tile-shape group of a step, forked from and joined back to the context's
+    // stream: the groups' launches run concurrently, so one's tail fills with the others' blocks
+    // and its own boundary-row scratch and slot pool
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gevents;   // [0]: fork, [1 + g]: group g done
+    std::deque<DevBuf> grows, gslots;
+    ~sw_server() {
+        for (cudaEvent_t e : gevents) if (e) cudaEventDestroy(e);
+        for (cudaStream_t t : gstreams) if (t) cudaStreamDestroy(t);
+    }
 };
 
 namespace {
@@ -241,9 +251,46 @@ extern "C" int sw_server_step(sw_server *S, int32_t *active) {
     if (chunk_pairs > 0) {
         DbView v = S->view;
         v.maxlen = std::max(1, db_chunk_maxlen(S->db, p0, p0 + 1));     // pairs are sorted longest first
-        for (const Launch &L : launches)
+        if (launches.size() == 1) {
+            const Launch &L = launches[0];
             RC(db_launch_shape(c, L.shape, static_cast<const DbJob *>(S->jobs.p) + L.job0, L.njobs, L.nblocks, v,
                                S->ds.K, L.maxm));
+        } else {
+            while (S->gstreams.size() < launches.size()) {
+                cudaStream_t t = nullptr;
+                CU(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+                S->gstreams.push_back(t);
+            }
+            while (S->grows.size() < launches.size()) {
+                S->grows.emplace_back();
+                S->gslots.emplace_back();
+            }
+            while (S->gevents.size() < launches.size() + 1) {
+                cudaEvent_t e = nullptr;
+                CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                S->gevents.push_back(e);
+            }
+            CU(cudaEventRecord(S->gevents[0], c->stream));
+            const cudaStream_t home = c->stream;
+            int rc = SW_OK;
+            for (size_t g = 0; g < launches.size() && rc == SW_OK; ++g) {
+                const Launch &L = launches[g];
+                const cudaStream_t gs = S->gstreams[g];
+                if (cudaStreamWaitEvent(gs, S->gevents[0], 0) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; break; }
+                c->stream = gs;
+                rc = db_launch_shape(c, L.shape, static_cast<const DbJob *>(S->jobs.p) + L.job0, L.njobs, L.nblocks,
+                                     v, S->ds.K, L.maxm, &S->grows[g], &S->gslots[g]);
+                c->stream = home;
+                if (rc == SW_OK && cudaEventRecord(S->gevents[1 + g], gs) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; }
+                if (rc == SW_OK && cudaStreamWaitEvent(home, S->gevents[1 + g], 0) != cudaSuccess) { cudaGetLastError(); rc = SW_ECUDA; }
+            }
+            c->stream = home;
+            if (rc != SW_OK) {
+                cudaStreamSynchronize(home);
+                for (cudaStream_t t : S->gstreams) cudaStreamSynchronize(t);
+                return rc;
+            }
+        }
     }
     CU(cudaMemcpyAsync(c->stage3.p, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
