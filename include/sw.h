@@ -297,13 +297,16 @@ int sw_dbsearch(sw_ctx *ctx, const sw_db *db, const uint8_t *q, int64_t m, const
  * searches (same results as sw_dbsearch for every request).
  *
  * The database is swept circularly in `chunks` pieces; every sw_server_step
- * runs the current piece for all admitted requests in one launch, so
- * requests that arrive while others are on the GPU share the device with
- * them.  A request is admitted by sw_server_submit when one of max_slots
- * slots (1..256) is free and its device memory (about 8 bytes per database
- * subject plus its query) fits mem_budget bytes, else SW_EAGAIN; it joins
- * the sweep at the next step and its hits are ready after `chunks` steps
- * (sw_server_poll: SW_EAGAIN while pending; a collected ticket is
+ * runs the current piece for all admitted requests at once, so requests
+ * that arrive while others are on the GPU share the device with them.
+ * Steps are pipelined: a step call enqueues its piece and then waits for
+ * the previous call's, so the device does not idle while the host admits
+ * and retires requests.  A request is admitted by sw_server_submit when one
+ * of max_slots slots (1..256) is free and its device memory (about 8 bytes
+ * per database subject plus its query) fits mem_budget bytes, else
+ * SW_EAGAIN; it joins the sweep at the next step call, and its hits are
+ * ready after `chunks` + 1 step calls, the last of which completes its last
+ * piece (sw_server_poll: SW_EAGAIN while pending; a collected ticket is
  * forgotten).  The scoring must allow the packed 16-bit search (every
  * S + gap_open within int8, penalties <= 16000), else SW_ERANGE at
  * creation; queries longer than 8000 give SW_ERANGE.  k <= 64.  A step runs
@@ -311,15 +314,20 @@ int sw_dbsearch(sw_ctx *ctx, const sw_db *db, const uint8_t *q, int64_t m, const
  * passes that fit it best).  A slot keeps its device buffers for the next
  * request, so the server holds at most max_slots of them; mem_used counts
  * the active requests' share.  A request whose retirement fails is
- * retired with that status (sw_server_poll returns it).  The server
- * uses its context's stream and must be destroyed before the context and
- * the database.
+ * retired with that status (sw_server_poll returns it); a device error in
+ * a step fails every request the server holds and every later call.  The
+ * server enqueues its admissions and retirements on its context's stream
+ * and its steps on streams of its own, with its own scoring table, error
+ * word and scratch, so the context's other calls may run between steps.
+ * It must be destroyed before the context and the database (destroying
+ * waits for a step in flight).
  */
 typedef struct sw_server sw_server;
 int sw_server_create(sw_ctx *ctx, const sw_db *db, const sw_scoring *sc, size_t mem_budget, int32_t k,
                      int32_t max_slots, int32_t chunks, sw_server **out);
 int sw_server_submit(sw_server *srv, const uint8_t *q, int64_t m, uint64_t *ticket);
-/* Run one sweep step (synchronous); *active = requests that took part. */
+/* Enqueue one sweep step, then complete the previous one (its finished
+ * requests retire); *active = requests in the enqueued step. */
 int sw_server_step(sw_server *srv, int32_t *active);
 int sw_server_poll(sw_server *srv, uint64_t ticket, sw_dbhit *hits, int32_t *nhits);
 /* Requests in flight, device bytes they hold, cells of retired requests. */

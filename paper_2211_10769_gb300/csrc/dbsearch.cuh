@@ -159,8 +159,10 @@ __device__ __forceinline__ void load_prof_words(const int8_t *p, uint32_t (&w)[d
     }
 }
 
-// grid: 1D; blocks [jobs[j].block0, jobs[j+1].block0) work on job j (the
-// host gives each job blocks in proportion to its work); block: W warps.
+// grid: 1D; blocks [jobs[j].block0, jobs[j+1].block0) start on job j (the
+// host gives each job blocks in proportion to its work); block: W warps.  A
+// block whose job has no pairs left moves on to the job of the launch with
+// the most work left (same scoring), so that the launch ends balanced.
 // Dynamic shared memory: the query profile, (K + 1) * mpad bytes,
 // mpad = passes * 32 * db_lane_slot(R) (lane slots of whole words).
 constexpr int kDbCH = 8;      // steps per chunk of the packed fill (steady chunks skip all range tests)
@@ -255,111 +257,132 @@ db_s16x2_kernel(const DbJob *__restrict__ jobs, int njobs, const DbView D,
         const int mid = (jlo + jhi + 1) >> 1;
         if (jobs[mid].block0 <= (int)blockIdx.x) jlo = mid; else jhi = mid - 1;
     }
-    const DbJob &J = jobs[jlo];
-    const DevScoring &SC = scorings[J.scoring];
-    const int K = SC.K, go = SC.go, ge = SC.ge;
-    const int m = J.m;
-    constexpr int ROWS = G * R;
-    constexpr int LS = db_lane_slot(R), PROWS = G * LS;    // profile bytes per lane and per pass
-    const int passes = (m + ROWS - 1) / ROWS;
-    const int mpad = passes * PROWS;
-    for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
-        const int r = i % LS, row = (i / PROWS) * ROWS + ((i % PROWS) / LS) * R + r;
-        const bool ok = r < R && row < m;
-        const int qc = ok ? min((int)J.q[row], K - 1) : 0;
-        for (int c = 0; c <= K; ++c)
-            prof[c * mpad + i] = (ok && c < K) ? (int8_t)(SC.mat[qc * K + c] + go) : (int8_t)kPadScore;
-    }
-    __syncthreads();
+    __shared__ int s_job;
+    for (int job = jlo; job >= 0;) {
+        const DbJob &J = jobs[job];
+        const DevScoring &SC = scorings[J.scoring];
+        const int K = SC.K, go = SC.go, ge = SC.ge;
+        const int m = J.m;
+        constexpr int ROWS = G * R;
+        constexpr int LS = db_lane_slot(R), PROWS = G * LS;    // profile bytes per lane and per pass
+        const int passes = (m + ROWS - 1) / ROWS;
+        const int mpad = passes * PROWS;
+        for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
+            const int r = i % LS, row = (i / PROWS) * ROWS + ((i % PROWS) / LS) * R + r;
+            const bool ok = r < R && row < m;
+            const int qc = ok ? min((int)J.q[row], K - 1) : 0;
+            for (int c = 0; c <= K; ++c)
+                prof[c * mpad + i] = (ok && c < K) ? (int8_t)(SC.mat[qc * K + c] + go) : (int8_t)kPadScore;
+        }
+        __syncthreads();
 
-    int maxs = 0;
-    for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
-    const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1), grp = lane / G;          // the lane's wavefront and its place there
-    const int gwarp = slot * W + (threadIdx.x >> 5);
-    uint2 *bnd = scratch + ((size_t)gwarp * NG + grp) * (size_t)(D.maxlen + 1);
-    const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
-    const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
+        int maxs = 0;
+        for (int k = 0; k < K * K; ++k) maxs = max(maxs, (int)SC.mat[k]);
+        const int tmax_u = 32767 - maxs - go;            // overflow threshold on H - open
+        const int lane = threadIdx.x & 31;
+        const int gl = lane & (G - 1), grp = lane / G;          // the lane's wavefront and its place there
+        const int gwarp = slot * W + (threadIdx.x >> 5);
+        uint2 *bnd = scratch + ((size_t)gwarp * NG + grp) * (size_t)(D.maxlen + 1);
+        const unsigned go2 = pack2(go, go), ge2 = pack2(ge, ge);
+        const unsigned ngo2 = pack2(-go, -go), nge2 = pack2(-ge, -ge), neg2 = pack2(kNeg16, kNeg16);
 
-    for (;;) {
-        // the warp takes NG consecutive pairs (similar lengths: the pairs are sorted), one per wavefront
-        int base = 0;
-        if (lane == 0) base = atomicAdd(J.next_pair, NG);
-        base = __shfl_sync(kFull, base, 0);
-        const int p = J.pair0 + (base + grp) * J.pair_stride;
-        const bool live = p < J.pair1;
-        if constexpr (NG == 1) {
-            if (!live) break;
-        } else {
-            if (!__any_sync(kFull, live)) break;
-        }
-        // a wavefront without a pair steps through no columns (its lanes still take part in the
-        // warp's shuffles); its residue pointer only has to be readable
-        int sa = -1, sb = -1, n = 0;
-        const uint16_t *pr = D.pres;
-        if (NG == 1 || live) {
-            sa = D.pairs[2 * p];
-            sb = D.pairs[2 * p + 1];
-            pr = D.pres + D.poff[p];
-            n = (int)(D.poff[p + 1] - D.poff[p]) - 1;           // columns (pr[n]: padding)
-        }
-        int nmax = n, nmin = n;                                  // over the warp's wavefronts
-        if constexpr (NG > 1) {
-            const int o = __shfl_xor_sync(kFull, n, G);
-            nmax = max(n, o);
-            nmin = min(n, o);
-        }
-        unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
-        for (int pass = 0; pass < passes; ++pass) {
-            DbLane<R> st;
-            st.prow = prof + pass * PROWS + gl * LS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) { st.U[r] = ngo2; st.E[r] = neg2; }
-            st.ub = ngo2; st.fb = neg2; st.udiag0 = ngo2;
-            st.cmax = cmax;
-            const bool last = pass + 1 == passes;
-            const bool tops = pass > 0;
-            // prefetched inputs of this lane's first column and of lane 0's first top cell
-            st.cp = gl == 0 && n > 0 ? pr[0] : 0xffffu;
-            st.topv = (tops && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
-            for (int s0 = 0; s0 < nmax + G - 1; s0 += kDbCH) {
-                if (s0 >= G - 1 && s0 + kDbCH <= nmin) {
-                    // steady state: every lane's column is inside its pair, the prefetched
-                    // column at most the padding column n
-#pragma unroll
-                    for (int k = 0; k < kDbCH; ++k)
-                        db_step<R, G, false>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
-                } else {
-                    for (int k = 0; k < kDbCH && s0 + k < nmax + G - 1; ++k)
-                        db_step<R, G, true>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+        for (;;) {
+            // the warp takes NG consecutive pairs (similar lengths: the pairs are sorted), one per wavefront
+            int base = 0;
+            if (lane == 0) base = atomicAdd(J.next_pair, NG);
+            base = __shfl_sync(kFull, base, 0);
+            const int p = J.pair0 + (base + grp) * J.pair_stride;
+            const bool live = p < J.pair1;
+            if constexpr (NG == 1) {
+                if (!live) break;
+            } else {
+                if (!__any_sync(kFull, live)) break;
+            }
+            // a wavefront without a pair steps through no columns (its lanes still take part in the
+            // warp's shuffles); its residue pointer only has to be readable
+            int sa = -1, sb = -1, n = 0;
+            const uint16_t *pr = D.pres;
+            if (NG == 1 || live) {
+                sa = D.pairs[2 * p];
+                sb = D.pairs[2 * p + 1];
+                pr = D.pres + D.poff[p];
+                n = (int)(D.poff[p + 1] - D.poff[p]) - 1;           // columns (pr[n]: padding)
+            }
+            int nmax = n, nmin = n;                                  // over the warp's wavefronts
+            if constexpr (NG > 1) {
+                const int o = __shfl_xor_sync(kFull, n, G);
+                nmax = max(n, o);
+                nmin = min(n, o);
+            }
+            unsigned cmax = ngo2;                                   // running max of H - open (H = 0)
+            for (int pass = 0; pass < passes; ++pass) {
+                DbLane<R> st;
+                st.prow = prof + pass * PROWS + gl * LS;
+    #pragma unroll
+                for (int r = 0; r < R; ++r) { st.U[r] = ngo2; st.E[r] = neg2; }
+                st.ub = ngo2; st.fb = neg2; st.udiag0 = ngo2;
+                st.cmax = cmax;
+                const bool last = pass + 1 == passes;
+                const bool tops = pass > 0;
+                // prefetched inputs of this lane's first column and of lane 0's first top cell
+                st.cp = gl == 0 && n > 0 ? pr[0] : 0xffffu;
+                st.topv = (tops && n > 0) ? bnd[0] : make_uint2(ngo2, neg2);
+                for (int s0 = 0; s0 < nmax + G - 1; s0 += kDbCH) {
+                    if (s0 >= G - 1 && s0 + kDbCH <= nmin) {
+                        // steady state: every lane's column is inside its pair, the prefetched
+                        // column at most the padding column n
+    #pragma unroll
+                        for (int k = 0; k < kDbCH; ++k)
+                            db_step<R, G, false>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+                    } else {
+                        for (int k = 0; k < kDbCH && s0 + k < nmax + G - 1; ++k)
+                            db_step<R, G, true>(st, s0 + k, gl, n, pr, bnd, tops, last, K, mpad, nge2, ngo2, neg2);
+                    }
+                }
+                cmax = st.cmax;
+                __syncwarp();
+            }
+            // each wavefront's maximum of each half
+            int ma = lo16(cmax), mb = hi16(cmax);
+    #pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                ma = max(ma, __shfl_xor_sync(kFull, ma, off));
+                mb = max(mb, __shfl_xor_sync(kFull, mb, off));
+            }
+            if (gl == 0 && (NG == 1 || live)) {
+                const int outs[2] = {sa, sb};
+                const int mx[2] = {ma, mb};
+                for (int h = 0; h < 2; ++h) {
+                    const int s = outs[h];
+                    if (s < 0) continue;
+                    if (mx[h] > tmax_u) {
+                        J.scores[s] = -1;
+                        const int slot = atomicAdd(J.novf, 1);
+                        J.ovf[slot] = s;
+                    } else {
+                        J.scores[s] = max(0, mx[h] + go);
+                    }
                 }
             }
-            cmax = st.cmax;
-            __syncwarp();
         }
-        // each wavefront's maximum of each half
-        int ma = lo16(cmax), mb = hi16(cmax);
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            ma = max(ma, __shfl_xor_sync(kFull, ma, off));
-            mb = max(mb, __shfl_xor_sync(kFull, mb, off));
-        }
-        if (gl == 0 && (NG == 1 || live)) {
-            const int outs[2] = {sa, sb};
-            const int mx[2] = {ma, mb};
-            for (int h = 0; h < 2; ++h) {
-                const int s = outs[h];
-                if (s < 0) continue;
-                if (mx[h] > tmax_u) {
-                    J.scores[s] = -1;
-                    const int slot = atomicAdd(J.novf, 1);
-                    J.ovf[slot] = s;
-                } else {
-                    J.scores[s] = max(0, mx[h] + go);
-                }
+        // this job has no pairs left: every warp is done with the profile; take the job of the
+        // launch with the most work left (pairs not yet claimed x passes), if any
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long best = 0;
+            int pick = -1;
+            for (int k = 0; k < njobs; ++k) {
+                const DbJob &O = jobs[k];
+                if (O.scoring != J.scoring) continue;
+                const int npairs = (O.pair1 - O.pair0 + O.pair_stride - 1) / O.pair_stride;
+                const int left = npairs - *(volatile const int32_t *)O.next_pair;
+                const long long work = (long long)left * ((O.m + ROWS - 1) / ROWS);
+                if (left > 0 && work > best) { best = work; pick = k; }
             }
+            s_job = pick;
         }
+        __syncthreads();
+        job = s_job;
     }
     if constexpr (OVERSUB) {                      // hand the slot to a later block
         __syncthreads();                          // every warp is done with the slot's scratch

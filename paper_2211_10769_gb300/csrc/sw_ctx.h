@@ -134,10 +134,18 @@ int db_shape(int K, int m);                // tile shape (index) for a query of 
 int db_shape_warps(int shape);
 int db_shape_rows(int shape);              // query rows per pass
 int db_resident_blocks_shape(sw_ctx *c, int shape, int K, int m, int *out);
-// rows / slots: the launch's boundary-row scratch and slot pool (default: the context's; launches that
-// run concurrently on different streams need their own)
+// Buffers of a database launch: boundary-row scratch, slot pool, scoring table and error word.
+// Default: the context's; launches that may run while other calls use the context (the
+// server's steps on their own streams) bring their own.
+struct DbBufs {
+    DevBuf *rows, *slots;
+    const DevScoring *scorings;
+    int *err;
+};
 int db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K, int m,
-                    DevBuf *rows = nullptr, DevBuf *slots = nullptr);
+                    const DbBufs *bufs = nullptr);
+// the scratch bytes db_launch_shape ensures for that launch (subjects up to maxlen residues)
+int db_scratch_shape(sw_ctx *c, int shape, int K, int m, int maxlen, size_t *row_bytes, size_t *slot_bytes);
 int db_resident_blocks(sw_ctx *c, int K, int m, int *out);
 int db_warps_per_block(int K, int m);
 int db_rows_per_pass(int K, int m);      // query rows per pass of the packed kernel for this launch shape

@@ -51,9 +51,10 @@ size_t db_profile_bytes(int K, int m) {
     return (size_t)(K + 1) * (size_t)mpad;
 }
 
+// Scratch of one launch: boundary rows, one per wavefront (32 / G of them a
+// warp) of every block that can be resident at once, and the slot pool's words.
 template <int R, int W, int G>
-int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m, DevBuf &rows,
-              DevBuf &slots) {
+int db_scratch(sw_ctx *c, int K, int m, int maxlen, int *nslots, size_t *row_bytes, size_t *slot_bytes) {
     const size_t smem = db_profile_bytes<R, G>(K, m);
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, db_s16x2_kernel<R, W, false, G>, W * 32, smem));
@@ -61,17 +62,27 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, db_s16x2_kernel<R, W, true, G>, W * 32, smem));
     occ = std::min(occ, occ2);
     if (occ < 1) return SW_ECUDA;
+    *nslots = occ * c->nsm;
+    *row_bytes = (size_t)*nslots * W * (32 / G) * (size_t)(maxlen + 1) * sizeof(uint2);
+    *slot_bytes = (size_t)((*nslots + 31) / 32) * sizeof(unsigned);
+    return SW_OK;
+}
+
+template <int R, int W, int G>
+int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView &D0, int K, int m,
+              const DbBufs &B) {
+    const size_t smem = db_profile_bytes<R, G>(K, m);
     // boundary rows: one per warp of every block that can be resident at once; a grid larger
     // than that (the server's steps) takes the kernel whose later blocks share the slots
     DbView D = D0;
-    D.nslots = occ * c->nsm;
+    size_t row_bytes = 0, slot_bytes = 0;
+    RC((db_scratch<R, W, G>(c, K, m, D.maxlen, &D.nslots, &row_bytes, &slot_bytes)));
     D.slot_words = (D.nslots + 31) / 32;
     const bool over = nblocks > D.nslots;
-    // (one boundary row per wavefront: 32 / G of them a warp)
-    RC(rows.ensure((size_t)D.nslots * W * (32 / G) * (size_t)(D.maxlen + 1) * sizeof(uint2)));
-    RC(slots.ensure((size_t)D.slot_words * sizeof(unsigned)));
-    D.slot_pool = static_cast<unsigned *>(slots.p);
-    D.err = static_cast<int *>(c->err.p);
+    RC(B.rows->ensure(row_bytes));
+    RC(B.slots->ensure(slot_bytes));
+    D.slot_pool = static_cast<unsigned *>(B.slots->p);
+    D.err = B.err;
     D.spin_limit = c->spin_limit;
     if (over) {
         init_slot_pool_kernel<<<1, 64, 0, c->stream>>>(D.slot_pool, D.slot_words, D.nslots, D.nslots);
@@ -80,9 +91,8 @@ int launch_db(sw_ctx *c, const DbJob *jobs, int njobs, int nblocks, const DbView
     }
     auto kern = over ? db_s16x2_kernel<R, W, true, G> : db_s16x2_kernel<R, W, false, G>;
     const int kp = kt_begin(c, SW_KT_DB16);
-    kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D,
-                                                         static_cast<const DevScoring *>(c->scorings.p),
-                                                         static_cast<uint2 *>(rows.p));
+    kern<<<(unsigned)nblocks, W * 32, smem, c->stream>>>(jobs, njobs, D, B.scorings,
+                                                         static_cast<uint2 *>(B.rows->p));
     kt_end(c, kp);
     CU(cudaGetLastError());
     ++c->launches;
@@ -182,11 +192,21 @@ int swgb::db_warps_per_block(int K, int m) { return db_shape_warps(db_shape(K, m
 int swgb::db_rows_per_pass(int K, int m) { return db_shape_rows(db_shape(K, m)); }
 
 int swgb::db_launch_shape(sw_ctx *c, int shape, const DbJob *jobs, int njobs, int nblocks, const DbView &D, int K,
-                          int m, DevBuf *rows, DevBuf *slots) {
-    DevBuf &r = rows ? *rows : c->dbscratch;
-    DevBuf &s = slots ? *slots : c->dbslots;
+                          int m, const DbBufs *bufs) {
+    DbBufs B{&c->dbscratch, &c->dbslots, static_cast<const DevScoring *>(c->scorings.p), static_cast<int *>(c->err.p)};
+    if (bufs) B = *bufs;
     switch (shape) {
-#define SWGB_DB_CASE(i, R, W, G) case i: return launch_db<R, W, G>(c, jobs, njobs, nblocks, D, K, m, r, s);
+#define SWGB_DB_CASE(i, R, W, G) case i: return launch_db<R, W, G>(c, jobs, njobs, nblocks, D, K, m, B);
+        SWGB_DB_SHAPES(SWGB_DB_CASE)
+#undef SWGB_DB_CASE
+        default: return SW_EINVAL;
+    }
+}
+
+int swgb::db_scratch_shape(sw_ctx *c, int shape, int K, int m, int maxlen, size_t *row_bytes, size_t *slot_bytes) {
+    int nslots = 0;
+    switch (shape) {
+#define SWGB_DB_CASE(i, R, W, G) case i: return db_scratch<R, W, G>(c, K, m, maxlen, &nslots, row_bytes, slot_bytes);
         SWGB_DB_SHAPES(SWGB_DB_CASE)
 #undef SWGB_DB_CASE
         default: return SW_EINVAL;

@@ -28,6 +28,9 @@ def _queries(n, seed):
 
 
 def test_alone_equals_mix(env):
+    """Requests arrive while others are in the sweep; between steps (with a
+    step in flight) the context also runs plain searches, which must not
+    disturb the server's buffers nor be disturbed by them."""
     ctx, pdb, db, binding = env
     sc = W.protein_scoring()
     qs = _queries(14, W.BASE_SEED + 810)
@@ -47,6 +50,9 @@ def test_alone_equals_mix(env):
                         break
                     tickets[t] = pending.pop(0)
         srv.step()
+        if step % 3 == 1:
+            qi = (step // 3) % len(qs)
+            assert db.search(qs[qi], sc.matrix, sc.gap_open, sc.gap_extend, k=20)[0] == alone[qi]
         for t, qi in list(tickets.items()):
             r = srv.poll(t)
             if r is not None:
@@ -74,6 +80,9 @@ def test_admission_by_slots_and_memory(env):
     assert srv.stats()[0] == 2
     for _ in range(3):
         srv.step()
+    # steps are pipelined: the third call enqueued the last chunk, the fourth completes it
+    assert srv.poll(t0) is None and srv.poll(t1) is None
+    srv.step()
     assert srv.poll(t0) is not None and srv.poll(t1) is not None
     assert srv.stats()[:2] == (0, 0)
     assert srv.submit(qs[2]) is not None             # admitted once memory is back
@@ -95,7 +104,7 @@ def test_serving_matches_oracle_and_rejects_bad_input(env, oracle_mod):
                          max_slots=4, chunks=4)
     qs = _queries(4, W.BASE_SEED + 840)
     ts = [srv.submit(q) for q in qs]
-    for _ in range(4):
+    for _ in range(4 + 1):
         srv.step()
     for t, q in zip(ts, qs):
         want = oracle_mod.top_k(oracle_mod.db_scores(q, small, sc.matrix, sc.gap_open, sc.gap_extend), 10)
