@@ -38,17 +38,21 @@ int launch16(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int max_b
     return SW_OK;
 }
 
-template <int R, int MODE, bool LEFT = false>
+template <int R, int MODE, bool LEFT = false, int W = 4>
 int launch16_pk(sw_ctx *c, const FillLaunch &L, int K, long long tickets, int B) {
-    if (p16_profile_bytes(R, 4, K, kP16Pair) <= kPairProfileMax)
-        return launch16<R, 4, MODE, kP16Pair, LEFT>(c, L, K, tickets, B);
-    return launch16<R, 4, MODE, kP16Int16, LEFT>(c, L, K, tickets, B);
+    if (p16_profile_bytes(R, W, K, kP16Pair) <= kPairProfileMax)
+        return launch16<R, W, MODE, kP16Pair, LEFT>(c, L, K, tickets, B);
+    return launch16<R, W, MODE, kP16Int16, LEFT>(c, L, K, tickets, B);
 }
 
 // left: the coarse-tile refills (checkpoint mode only), whose tasks enter the
-// fill at a checkpoint column.
+// fill at a checkpoint column.  W = 2 (score mode only): blocks of two compute
+// warps for batches, whose pairs' last strips are partly empty (a strip of
+// four warps runs its pair's width with one to four of them busy).
 template <int R>
-int launch16_mode(sw_ctx *c, int mode, bool left, const FillLaunch &L, int K, long long tickets, int B) {
+int launch16_mode(sw_ctx *c, int mode, bool left, int W, const FillLaunch &L, int K, long long tickets, int B) {
+    if (W == 2) return mode == kModeScore && !left ? launch16_pk<R, kModeScore, false, 2>(c, L, K, tickets, B) : SW_EINVAL;
+    if (W != 4) return SW_EINVAL;
     if (left) return mode == kModeScoreCk ? launch16_pk<R, kModeScoreCk, true>(c, L, K, tickets, B) : SW_EINVAL;
     switch (mode) {
         case kModeScore: return launch16_pk<R, kModeScore>(c, L, K, tickets, B);
@@ -70,11 +74,10 @@ bool swgb::p16_fits(const DevScoring &s, int R) {
 int swgb::launch_fill16(sw_ctx *c, const FillConfig &cfg, int mode, const FillLaunch &L, int K,
                         long long tickets) {
     if (tickets <= 0) return SW_OK;
-    if (cfg.W != 4) return SW_EINVAL;
     switch (cfg.R) {
-        case 8: return launch16_mode<8>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
-        case 12: return launch16_mode<12>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
-        case 16: return launch16_mode<16>(c, mode, cfg.left != 0, L, K, tickets, cfg.B);
+        case 8: return launch16_mode<8>(c, mode, cfg.left != 0, cfg.W, L, K, tickets, cfg.B);
+        case 12: return launch16_mode<12>(c, mode, cfg.left != 0, cfg.W, L, K, tickets, cfg.B);
+        case 16: return launch16_mode<16>(c, mode, cfg.left != 0, cfg.W, L, K, tickets, cfg.B);
         default: return SW_EINVAL;
     }
 }

@@ -64,22 +64,23 @@ def test_batch_matches_oracle(ctx, oracle_mod, flags):
     plan.close()
 
 
-@pytest.mark.parametrize("R", [8, 12, 16])
-def test_batch_packed_lanes(oracle_mod, monkeypatch, R):
+@pytest.mark.parametrize("R,Wc", [(8, 4), (12, 4), (16, 4), (8, 2), (12, 2), (16, 2)])
+def test_batch_packed_lanes(oracle_mod, monkeypatch, R, Wc):
     """Bins forced onto the packed 16-bit fill (both alphabets keep it exact at
-    these strip heights): every pair's score and end cell equal the oracle's,
-    including pairs that span several strips."""
+    these strip heights), in blocks of four or two compute warps: every pair's
+    score and end cell equal the oracle's, including pairs that span several
+    strips and last strips that leave warps without rows."""
     from paper_2211_10769_gb300 import binding
-    monkeypatch.setenv("SWGB_BATCH", "%d,4,1" % R)
+    monkeypatch.setenv("SWGB_BATCH", "%d,%d,1" % (R, Wc))
     c = binding.Context(0)
     try:
         sc = _scorings()
         pairs = _mixed_pairs(W.BASE_SEED + 12100 + R, 160, hi=4500)
-        assert sum(len(a) > 32 * 4 * R for a, _, _ in pairs) >= 3
+        assert sum(len(a) > 32 * Wc * R for a, _, _ in pairs) >= 3
         want = _oracle_hits(oracle_mod, pairs, sc)
         plan = binding.Batch(c, pairs, sc, flags=0)
         bins = plan.bins()
-        assert bins and all(lb == 16 and r == R for r, _, lb, _ in bins), bins
+        assert bins and all(lb == 16 and r == R and w == Wc for r, w, lb, _ in bins), bins
         got = plan.run()
         assert [(h.score, h.a_end, h.b_end) for h in got] == want
         plan.close()
