@@ -411,7 +411,8 @@ extern "C" int sw_batch_create(sw_ctx *c, int64_t npairs, const uint8_t *a_res, 
         std::stable_sort(bins.begin(), bins.end(), [&](const Bin &x, const Bin &y) { return bin_cells(x) > bin_cells(y); });
         for (Bin &bin : bins) {
             bin.cfg = c->bat;
-            if (bin.cfg.P16 && (bin.cfg.W != 4 || !p16_fits(B->scorings[(size_t)bin.sidx], bin.cfg.R))) bin.cfg.P16 = 0;
+            if (bin.cfg.P16 && ((bin.cfg.W != 4 && bin.cfg.W != 2) || !p16_fits(B->scorings[(size_t)bin.sidx], bin.cfg.R)))
+                bin.cfg.P16 = 0;
             if (B->scorings[(size_t)bin.sidx].alg != kAlgLocal) {   // global, semi-global, overlap
                 bin.cfg = FillConfig{bin.rclass ? 16 : 8, 4};
                 bin.cfg.alg = 1;

@@ -218,13 +218,15 @@ __device__ __forceinline__ void p16_step(P16Lane<R> &st, const uint32_t (&pw)[R 
     if (lane == 31)      // the warp's bottom row (H - open, F) at column s - 63, scaled absolute
         rout[(j - 1) & (QS - 1)] = make_int2(p16_hi(st.ub) + st.B, p16_hi(f) + st.B);
     // keys: value | (7 - k) in both halves; the column's largest key
-    unsigned ck = __vimax3_s16x2(st.U[0] | 0x00070007u, st.U[1] | 0x00060006u, st.U[2] | 0x00050005u);
+    // (the low 3 bits of a scaled value are 0, so adding the tag sets them without a carry: an
+    // integer add, which the FMA pipe takes, instead of an OR on the busier ALU pipe)
+    unsigned ck = __vimax3_s16x2(st.U[0] + 0x00070007u, st.U[1] + 0x00060006u, st.U[2] + 0x00050005u);
 #pragma unroll
     for (int k = 3; k < H; k += 2) {
         const unsigned t0 = (unsigned)(7 - k) * 0x00010001u;
         const int k1 = k + 1 < H ? k + 1 : k;
         const unsigned t1 = (unsigned)(7 - k1) * 0x00010001u;
-        ck = __vimax3_s16x2(ck, st.U[k] | t0, st.U[k1] | t1);
+        ck = __vimax3_s16x2(ck, st.U[k] + t0, st.U[k1] + t1);
     }
     if (TAIL) ck = p16_pack(j < n ? p16_lo(ck) : -32768, j - 1 < n ? p16_hi(ck) : -32768);
     bool ph, pl;
