@@ -52,6 +52,7 @@ struct TileTable {
     int32_t I0, J0, nI, nJ;
     int32_t BT;                // tile side
     int32_t R;                 // rows per word
+    int32_t win_groups;        // row groups of a window (walk_window_groups)
 };
 
 constexpr int kLook = 2;              // groups of 32 cells each lane reads ahead per iteration
@@ -63,7 +64,15 @@ constexpr int kStageThreads = 256;    // threads staging a window (warps 1..8)
 constexpr int kWalkThreads = 32 + kStageThreads;   // warp 0 walks
 constexpr int kStage = 16;            // window words a thread loads at once
 constexpr int kWinMargin = 16;        // columns a staged window must leave either side of the walk's cell
-constexpr int kWalkMinBT = 1024;      // tiles at least this side: a window meets 2 x 2 tiles at most
+constexpr int kWalkMinBT = 512;       // tiles at least this side
+
+// Row groups of a window on tiles of side BT: its rows, and its band of
+// columns ((groups - 1) R + kWinCols wide), each within BT, so that a window
+// meets 2 x 2 tiles at most (768 rows on tiles of 1,024 and more).
+__host__ __device__ constexpr int walk_min3(int a, int b, int c) { return a < b ? (a < c ? a : c) : (b < c ? b : c); }
+__host__ __device__ constexpr int walk_window_groups(int BT, int R) {
+    return walk_min3(kWinRows / R, BT / R, (BT - kWinCols) / R + 1);
+}
 
 template <int R>
 constexpr size_t walk_window_bytes(size_t word_bytes) { return 2 * (size_t)(kWinRows / R) * kWinCols * word_bytes; }
@@ -94,7 +103,7 @@ __device__ __forceinline__ const Word *tile_ptr(const TileTable<Word> &T, const 
 // on in that group.
 template <typename Word, int R>
 __device__ WalkWindow make_window_g(const TileTable<Word> &T, const Word *const *tiles, int ghi, int chi) {
-    constexpr int RG = kWinRows / R;
+    const int RG = T.win_groups;
     constexpr int kNone = 0x7fffffff;
     WalkWindow m;
     const int glo = max(0, ghi - (RG - 1));
@@ -217,7 +226,8 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const TileTable<W
     if (blockIdx.x != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntab = T.nI * T.nJ;
-    if (ntab > kWalkTableMax || T.BT < kWalkMinBT) {     // the host keeps bands and tiles within these
+    if (ntab > kWalkTableMax || T.BT < kWalkMinBT || T.win_groups < 1 || T.win_groups > kWinRows / R ||
+        T.win_groups != walk_window_groups(T.BT, R)) {   // the host keeps bands, tiles and windows within these
         if (threadIdx.x == 0) st->done = 2;
         return;
     }
