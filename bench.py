@@ -42,8 +42,8 @@ WORKLOAD = "dna_pair_200kbp_align"
 # DRAM traffic of the forward fill measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one full-size launch) per cell, and the kernel
 # sources it was taken on (None: not measured on the current kernel).
-FILL_TRAFFIC = {"mode": "align", "bytes_per_cell": 394.86e6 / (200_000 * 200_000),
-                "source_sha256": "77223e02c53dfcce8e0e843ad996f8f1142c8121b2ddebfb5ab3e4d226828f7a"}
+FILL_TRAFFIC = {"mode": "align", "bytes_per_cell": 395.31e6 / (200_000 * 200_000),
+                "source_sha256": "3f0f0a5b28f5ef9f15e8d489472384b80bb35c223c097b602f4424626c8cbfac"}
 
 
 def parse():
