@@ -433,7 +433,7 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     if (const char *f = std::getenv("SWGB_TB")) std::sscanf(f, "%d,%d", &c->tbc.R, &c->tbc.W);
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d,%d", &c->bat.R, &c->bat.W, &c->bat.P16);
     if (const char *f = std::getenv("SWGB_PROF32")) c->prof32 = std::atoi(f) != 0;
-    if (const char *f = std::getenv("SWGB_ONE_ROUND")) c->one_round = std::atoi(f) != 0;
+    if (const char *f = std::getenv("SWGB_ONE_ROUND")) c->one_round = std::atoi(f) != 0 ? 1 : 0;
     if (const char *f = std::getenv("SWGB_TWO_LEVEL")) std::sscanf(f, "%lld,%lld", &c->two_level_bt1, &c->two_level_bt2);
     if (const char *f = std::getenv("SWGB_P16")) c->p16 = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);

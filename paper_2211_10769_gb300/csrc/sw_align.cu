@@ -211,72 +211,129 @@ int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t 
     return SW_OK;
 }
 
-// Sides up to this many cells take the one-round reconstruction below.
+// Sides up to this many cells may take the one-round reconstruction below.
 constexpr int64_t kOneRoundSide = 8192;
 
-// Reconstruction of a small pair in one round, with one host synchronisation:
-// the score fill (end-cell candidates) and a traceback fill of the whole
-// matrix as a single BT x BT tile, the end cell reduced on the device, the walk
-// started from it there (walk_start_kernel), and every result copied back at
-// once.  The decision bits of the whole matrix cost BT * BT / 2 bytes (32 MB at
-// the largest side); in exchange there are no checkpoints, no bands and no
-// host round trips between the steps, which dominate small pairs.
-int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, int64_t n, const DevScoring &ds,
-                    bool fold, sw_alignment *out) {
+// Tile side of a small pair's reconstruction: a multiple of both fills' strip
+// heights and of the chunk, at least kWalkMinBT; 0 if none fits.
+long long small_pair_tile(const sw_ctx *c, int64_t m, const DevScoring &ds, FillConfig *fwd_out, FillConfig *tbc_out,
+                          int *sw_out) {
     const FillConfig fwd = pair_fill_config_for(c, m, ds);
     const int sw = pair_strip_warps(c, fwd, m);
     const int HC = sw * 32 * fwd.R;
-    FillConfig tbc = c->tbc;
+    // the traceback tiles continue the forward fill's staircase checkpoint columns lane by
+    // lane, so both fills must give each lane the same rows (R)
+    FillConfig tbc = (c->tbc.R == fwd.R && fwd.alg == kAlgLocal) ? c->tbc : FillConfig{fwd.R, 4};
     tbc.P16 = 0;
-    tbc.alg = ds.alg;
-    if (ds.alg != kAlgLocal && tbc.R != 8 && tbc.R != 12 && tbc.R != 16) tbc.R = 8;
+    tbc.alg = fwd.alg;
+    const long long BL = std::lcm((long long)HC, (long long)fill_rows_per_strip(tbc));
+    const long long BT = BL * ((kWalkMinBT + BL - 1) / BL);
+    if (BT % kCH != 0) return 0;
+    *fwd_out = fwd;
+    *tbc_out = tbc;
+    *sw_out = sw;
+    return BT;
+}
+
+// Reconstruction of a small pair in one round, with one host synchronisation:
+// the forward fill with checkpoints every BT rows and columns, the end cell
+// reduced on the device, every BT x BT traceback tile of the matrix
+// recomputed from those checkpoints in one launch (independent tasks), the
+// walk started from the end cell there (walk_start_kernel) through a table of
+// all tiles, and every result copied back at once.  The banded path needs a
+// host round trip between the end cell and its band; for a pair whose tiles
+// fit one wave on the SMs, recomputing all of them costs no more time.
+int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, int64_t n, const DevScoring &ds,
+                    bool fold, const FillConfig &fwd, const FillConfig &tbc, int sw, long long BT, sw_alignment *out) {
+    const int HC = sw * 32 * fwd.R;
     const int R = tbc.R;
+    const int aux_rows = fwd.P16 ? fwd.R / 2 : fwd.R;
     const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
     const int HS = tsw * 32 * R;
-    // one tile holds the whole matrix: its side is a multiple of R and of 64, at least kWalkMinBT
-    long long BT = std::max<long long>(std::max(m, n), kWalkMinBT);
-    BT = (BT + 63) / 64 * 64;
-    BT = (BT + R - 1) / R * R;
-    const size_t tile_bytes = (size_t)((BT + R - 1) / R) * (size_t)BT * (size_t)tb_word_bytes(R);
+    if (BT % HC != 0 || BT % HS != 0) return SW_EINVAL;
+    const int nI = (int)((m + BT - 1) / BT), nJ = (int)((n + BT - 1) / BT);
+    // the walk's table: row ti keeps tile columns [ti + J0, ti + J0 + nJw) (its diagonal layout),
+    // J0 = 1 - nI and nJw = nI + nJ - 1 columns, so that every row holds all of its tiles
+    const int J0 = 1 - nI, nJw = nI + nJ - 1;
+    if ((long long)nI * nJw > kWalkTableMax) return SW_EINVAL;
+    const int ntiles = nI * nJ;
+    const size_t tile_bytes = (size_t)(BT / R) * (size_t)BT * (size_t)tb_word_bytes(R);
+    const long long nrowck = std::max<long long>(1, m / BT), ncolck = std::max<long long>(1, n / BT);
 
-    FillTask t{};                                   // the score fill
+    FillTask t{};                                   // the forward fill, checkpoints every BT
     t.a = da; t.b = db;
     t.rows = (int32_t)m; t.ncols = (int32_t)n;
     t.strip_warps = sw;
     t.nstrips = (int32_t)((m + HC - 1) / HC);
     t.nslot = std::min(t.nstrips, 4);
-    FillTask u{};                                   // the traceback fill, one tile
-    u.a = da; u.b = db;
-    u.rows = (int32_t)m; u.ncols = (int32_t)n;
-    u.strip_warps = tsw;
-    u.nstrips = (int32_t)((m + HS - 1) / HS);
-    u.nslot = std::min(u.nstrips, 4);
-    u.tb_ld = BT;
-    RC(c->bnd.ensure((size_t)(t.nslot + u.nslot) * (size_t)n * sizeof(int2)));
+    RC(c->bnd.ensure((size_t)t.nslot * (size_t)n * sizeof(int2)));
     t.bnd = static_cast<int2 *>(c->bnd.p);
-    u.bnd = t.bnd + (size_t)t.nslot * (size_t)n;
-    RC(c->tb.ensure(tile_bytes));
-    u.tb = c->tb.p;
-    const long long tickets = (long long)t.nstrips + u.nstrips;
-    RC(c->tasks.ensure(2 * sizeof(FillTask)));
-    RC(c->prog.ensure((size_t)tickets * sizeof(int)));
-    RC(c->cand.ensure((size_t)tickets * sizeof(int4)));
+    t.ckpt_every = (int32_t)(BT / HC);
+    RC(c->ckpt.ensure((size_t)nrowck * (size_t)n * sizeof(int2)));
+    t.ckpt = static_cast<int2 *>(c->ckpt.p);
+    t.colck_every = (int32_t)BT;
+    t.colck_ld = (long long)t.nstrips * HC;     // rows padded to whole strips (the padding is written)
+    RC(c->colck.ensure((size_t)ncolck * (size_t)t.colck_ld * sizeof(int2)));
+    RC(c->colaux.ensure((size_t)ncolck * (size_t)(t.colck_ld / aux_rows) * sizeof(int2)));
+    t.colck = static_cast<int2 *>(c->colck.p);
+    t.colck_aux = static_cast<int2 *>(c->colaux.p);
+    const int2 *rowck = t.ckpt, *colck = t.colck, *colaux = t.colck_aux;
+    const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / aux_rows;
+
+    RC(c->tb.ensure((size_t)ntiles * tile_bytes));
+    RC(c->tbbnd.ensure((size_t)ntiles * 2 * (size_t)BT * sizeof(int2)));
+    std::vector<FillTask> tasks;                    // [0]: the forward fill; then every tile
+    tasks.reserve((size_t)ntiles + 1);
+    tasks.push_back(t);
+    std::vector<const void *> table((size_t)nI * nJw, nullptr);
+    long long tickets = 0;
+    for (int ti = 0; ti < nI; ++ti)
+        for (int tj = 0; tj < nJ; ++tj) {
+            FillTask u{};
+            const long long r0 = (long long)ti * BT, c0 = (long long)tj * BT;
+            u.a = da + r0;
+            u.b = db + c0;
+            u.rows = (int32_t)std::min<long long>(BT, m - r0);
+            u.ncols = (int32_t)std::min<long long>(BT, n - c0);
+            u.strip_warps = tsw;
+            u.nstrips = (u.rows + HS - 1) / HS;
+            u.ticket0 = tickets;
+            u.top = r0 == 0 ? nullptr : rowck + (size_t)(r0 / BT - 1) * n + c0;
+            if (c0 > 0) {
+                u.left = colck + (size_t)(c0 / BT - 1) * colck_ld + r0;
+                u.left_aux = colaux + (size_t)(c0 / BT - 1) * colaux_ld + r0 / aux_rows;
+                u.left_split = fwd.P16 ? 1 : 0;
+            }
+            const size_t k = tasks.size() - 1;
+            u.nslot = std::min(u.nstrips, 2);
+            u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;
+            u.row0 = (int32_t)r0;
+            u.col0 = (int32_t)c0;
+            u.tb = static_cast<char *>(c->tb.p) + k * tile_bytes;
+            u.tb_ld = BT;
+            tickets += u.nstrips;
+            tasks.push_back(u);
+            table[(size_t)ti * nJw + (size_t)(tj - J0 - ti)] = u.tb;
+        }
+    const long long all = (long long)t.nstrips + tickets;
+    RC(c->tasks.ensure(tasks.size() * sizeof(FillTask)));
+    RC(c->prog.ensure((size_t)all * sizeof(int)));
+    RC(c->cand.ensure((size_t)all * sizeof(int4)));
     RC(c->ticket.ensure(2 * sizeof(unsigned long long)));
     RC(c->result.ensure(sizeof(int4)));
     RC(c->walk.ensure(sizeof(WalkState)));
     RC(c->runs.ensure((size_t)(m + n + 2) * sizeof(int2)));
-    RC(c->misc.ensure(sizeof(void *)));
-    // host staging: the two tasks and the one-entry tile table go down in two copies
-    const size_t tab_off = (2 * sizeof(FillTask) + 15) / 16 * 16;
-    RC(c->stage.ensure(tab_off + sizeof(void *)));
-    std::memcpy(c->stage.p, &t, sizeof(t));
-    std::memcpy(static_cast<char *>(c->stage.p) + sizeof(FillTask), &u, sizeof(u));
-    const void *tile = c->tb.p;
-    std::memcpy(static_cast<char *>(c->stage.p) + tab_off, &tile, sizeof(tile));
-    CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, 2 * sizeof(FillTask), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(c->misc.p, static_cast<char *>(c->stage.p) + tab_off, sizeof(void *),
+    RC(c->misc.ensure(table.size() * sizeof(void *)));
+    // host staging: the tasks and the tile table go down in two copies
+    const size_t task_bytes = tasks.size() * sizeof(FillTask);
+    const size_t tab_off = (task_bytes + 15) / 16 * 16;
+    RC(c->stage.ensure(tab_off + table.size() * sizeof(void *)));
+    std::memcpy(c->stage.p, tasks.data(), task_bytes);
+    std::memcpy(static_cast<char *>(c->stage.p) + tab_off, table.data(), table.size() * sizeof(void *));
+    CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, task_bytes, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->misc.p, static_cast<char *>(c->stage.p) + tab_off, table.size() * sizeof(void *),
                        cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemsetAsync(c->prog.p, 0, (size_t)tickets * sizeof(int), c->stream));
+    CU(cudaMemsetAsync(c->prog.p, 0, (size_t)all * sizeof(int), c->stream));
     CU(cudaMemsetAsync(c->ticket.p, 0, 2 * sizeof(unsigned long long), c->stream));
 
     const FillTask *dtasks = static_cast<const FillTask *>(c->tasks.p);
@@ -290,24 +347,25 @@ int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, 
     L.total = t.nstrips;
     L.spin_limit = c->spin_limit;
     L.ntasks = 1;
-    RC(launch_fill(c, fwd, kModeScore, fold, L, ds.K, t.nstrips));
+    RC(launch_fill(c, fwd, kModeScoreCk, fold, L, ds.K, t.nstrips));
     reduce_candidates_kernel<<<1, 32, 0, c->stream>>>(dtasks, 1, static_cast<const int4 *>(c->cand.p),
                                                        static_cast<const DevScoring *>(c->scorings.p),
                                                        static_cast<int4 *>(c->result.p));
     CU(cudaGetLastError());
     ++c->launches;
-    FillLaunch Lt = L;                              // the traceback fill: its own tickets and progress
+    FillLaunch Lt = L;                              // the tiles: their own tickets and progress
     Lt.tasks = dtasks + 1;
     Lt.ticket = static_cast<unsigned long long *>(c->ticket.p) + 1;
     Lt.prog = static_cast<int *>(c->prog.p) + t.nstrips;
     Lt.cand = static_cast<int4 *>(c->cand.p) + t.nstrips;
-    Lt.total = u.nstrips;
-    RC(launch_fill(c, tbc, kModeTb, fold, Lt, ds.K, u.nstrips));
+    Lt.total = tickets;
+    Lt.ntasks = ntiles;
+    RC(launch_fill(c, tbc, kModeTb, fold, Lt, ds.K, tickets));
     walk_start_kernel<<<1, 32, 0, c->stream>>>(static_cast<const int4 *>(c->result.p), ds.alg == kAlgLocal ? 1 : 0,
                                                static_cast<WalkState *>(c->walk.p));
     CU(cudaGetLastError());
     ++c->launches;
-    RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), 0, 0, 1, 1, (int)BT, R));
+    RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), 0, J0, nI, nJw, (int)BT, R));
 
     // everything back at once: end cell, walk state, error word, run records
     const size_t runs_off = 128;
@@ -328,7 +386,7 @@ int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, 
     RC(map_kernel_error(e));
     if (ds.alg == kAlgLocal && res.x <= 0) return empty_alignment(out);
     if (res.y == 0 || res.z == 0) return border_alignment(ds.alg, res.x, res.y, res.z, out);
-    if (w.done != 1 || w.nruns < 0 || w.nruns > m + n) return SW_ECUDA;   // one tile holds every cell
+    if (w.done != 1 || w.nruns < 0 || w.nruns > m + n) return SW_ECUDA;   // every tile is in the table
     return finish_alignment(ds.alg, res.x, res.y, res.z, w, reinterpret_cast<const int2 *>(h + runs_off), out);
 }
 
@@ -357,7 +415,15 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     RC(validate_codes(c, db, n, ds.K));
     RC(upload_scorings(c, {ds}));
     const bool fold = fold_open(ds);
-    if (c->one_round && std::max(m, n) <= kOneRoundSide) return align_one_round(c, da, m, db, n, ds, fold, out);
+    if (c->one_round != 0 && std::max(m, n) <= kOneRoundSide) {
+        // one round: forced (one_round > 0), or by default where every tile fits one wave on the SMs
+        FillConfig f1{8, 4}, t1{8, 4};
+        int sw1 = 4;
+        const long long bt = small_pair_tile(c, m, ds, &f1, &t1, &sw1);
+        const long long tiles = bt > 0 ? ((m + bt - 1) / bt) * ((n + bt - 1) / bt) : 0;
+        if (bt > 0 && (c->one_round > 0 || tiles <= c->nsm))
+            return align_one_round(c, da, m, db, n, ds, fold, f1, t1, sw1, bt, out);
+    }
 
     // ---- tile side: both checkpoint sets within the budget
     // tiles are BT x BT; BT is a multiple of both fills' strip heights, so

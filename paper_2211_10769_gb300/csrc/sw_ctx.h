@@ -77,7 +77,7 @@ struct sw_ctx {
     bool prof32 = true;               // int32 query profiles where they fit (small alphabets)
     bool p16 = true;                  // packed 16-bit pair fill where it is exact (p16_fits)
     int tb_band = 0;                  // tile rows per traceback band (0 = about one tile per SM)
-    bool one_round = false;           // sw_align of small pairs in one round (whole-matrix traceback bits)
+    int one_round = -1;               // sw_align of small pairs in one round: 1 forced, 0 off, -1 where the tiles fit one wave
     long long two_level_bt1 = 0;      // sw_align: forced coarse / fine checkpoint sides (0 = by budget)
     long long two_level_bt2 = 0;
     int tb_strip_warps = 0;           // compute warps per traceback strip (0 = all)

@@ -117,3 +117,34 @@ def test_serving_matches_oracle_and_rejects_bad_input(env, oracle_mod):
         srv.poll(123456)
     srv.close()
     sdb.close()
+
+
+def test_destroy_with_a_step_in_flight(env, oracle_mod):
+    """Steps are pipelined: after a step call the step it enqueued is still on
+    the device.  Destroying the server then waits for it; the context and the
+    database stay usable, and a new server gives the oracle's hits."""
+    ctx, pdb, db, binding = env
+    sc = W.protein_scoring()
+    qs = _queries(3, W.BASE_SEED + 850)
+    srv = binding.Server(ctx, db, sc.matrix, sc.gap_open, sc.gap_extend, mem_budget=1 << 30, k=5,
+                         max_slots=4, chunks=3)
+    for q in qs:
+        assert srv.submit(q) is not None
+    assert srv.step() == 3                    # one chunk of each request enqueued
+    srv.close()
+    small = [pdb.subject(s) for s in range(200)]
+    off = np.zeros(201, np.int64)
+    np.cumsum([len(x) for x in small], out=off[1:])
+    sdb = binding.Database(ctx, np.concatenate(small), off)
+    srv = binding.Server(ctx, sdb, sc.matrix, sc.gap_open, sc.gap_extend, mem_budget=1 << 28, k=5,
+                         max_slots=2, chunks=2)
+    t = srv.submit(qs[0])
+    steps = 0
+    while (hits := srv.poll(t)) is None:
+        srv.step()
+        steps += 1
+        assert steps < 10
+    assert steps == 3                         # chunks + 1 step calls
+    assert hits == oracle_mod.top_k(oracle_mod.db_scores(qs[0], small, sc.matrix, sc.gap_open, sc.gap_extend), 5)
+    srv.close()
+    sdb.close()
