@@ -185,7 +185,10 @@ int sw_score(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t
  * Resolution and reconstruction for one pair (paper Section 2.2): score,
  * canonical alignment path and coordinates.  Same limits as sw_score.  The
  * path is reconstructed from traceback bits recomputed on the device from
- * checkpoint rows, so device memory stays far below the m*n matrix.
+ * checkpoint rows, so device memory stays far below the m*n matrix.  A pair
+ * whose traceback tiles fit one wave on the SMs (sides up to 8,192) is
+ * reconstructed with one host synchronisation; larger pairs take bands of
+ * tiles along the path, one synchronisation per band.
  * *out is written only on success; release it with sw_alignment_free.
  */
 int sw_align(sw_ctx *ctx, const uint8_t *a, int64_t m, const uint8_t *b, int64_t n,
