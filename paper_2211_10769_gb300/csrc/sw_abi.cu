@@ -317,33 +317,45 @@ int swgb::launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, con
     return SW_EINVAL;
 }
 
-// Runs the fill over `tasks` (already in host memory, ticket0 assigned) and
-// leaves the per-strip candidates in c->cand.
-int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
-                   const std::vector<FillTask> &tasks, long long tickets, int K) {
+// Runs the fill over `tasks` (already in host memory, ticket0 assigned) on
+// stream st with buffers b, and leaves the per-strip candidates in b.cand.
+int swgb::run_fill_with(sw_ctx *c, const FillBufs &b, cudaStream_t st, const FillConfig &cfg, int mode, bool fold,
+                        const std::vector<FillTask> &tasks, long long tickets, int K) {
     const size_t tbytes = tasks.size() * sizeof(FillTask);
-    RC(c->tasks.ensure(tbytes));
-    RC(c->prog.ensure((size_t)tickets * sizeof(int)));
-    RC(c->cand.ensure((size_t)tickets * sizeof(int4)));
-    RC(c->ticket.ensure(sizeof(unsigned long long)));
-    RC(c->stage.ensure(tbytes));
-    std::memcpy(c->stage.p, tasks.data(), tbytes);
-    CU(cudaMemcpyAsync(c->tasks.p, c->stage.p, tbytes, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemsetAsync(c->prog.p, 0, (size_t)tickets * sizeof(int), c->stream));
-    CU(cudaMemsetAsync(c->ticket.p, 0, sizeof(unsigned long long), c->stream));
+    RC(b.tasks->ensure(tbytes));
+    RC(b.prog->ensure((size_t)tickets * sizeof(int)));
+    RC(b.cand->ensure((size_t)tickets * sizeof(int4)));
+    RC(b.ticket->ensure(sizeof(unsigned long long)));
+    RC(b.stage->ensure(tbytes));
+    std::memcpy(b.stage->p, tasks.data(), tbytes);
+    CU(cudaMemcpyAsync(b.tasks->p, b.stage->p, tbytes, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(b.prog->p, 0, (size_t)tickets * sizeof(int), st));
+    CU(cudaMemsetAsync(b.ticket->p, 0, sizeof(unsigned long long), st));
     FillLaunch L{};
-    L.tasks = static_cast<const FillTask *>(c->tasks.p);
+    L.tasks = static_cast<const FillTask *>(b.tasks->p);
     L.scorings = static_cast<const DevScoring *>(c->scorings.p);
-    L.ticket = static_cast<unsigned long long *>(c->ticket.p);
-    L.prog = static_cast<int *>(c->prog.p);
-    L.cand = static_cast<int4 *>(c->cand.p);
+    L.ticket = static_cast<unsigned long long *>(b.ticket->p);
+    L.prog = static_cast<int *>(b.prog->p);
+    L.cand = static_cast<int4 *>(b.cand->p);
     L.err = static_cast<int *>(c->err.p);
     L.total = tickets;
     L.spin_limit = c->spin_limit;
     L.ntasks = (int)tasks.size();
-    // c->stage is pinned and copied asynchronously: callers synchronise the
-    // stream before they run another fill (every ABI call ends with a sync).
-    return launch_fill(c, cfg, mode, fold, L, K, tickets);
+    // the staging buffer is pinned and copied asynchronously: callers synchronise the stream
+    // before they stage another fill on the same buffers (every ABI call ends with a sync)
+    const cudaStream_t home = c->stream;
+    c->stream = st;
+    const int rc = launch_fill(c, cfg, mode, fold, L, K, tickets);
+    c->stream = home;
+    return rc;
+}
+
+// Runs the fill over `tasks` on the context's stream and buffers; the
+// per-strip candidates are left in c->cand.
+int swgb::run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold,
+                   const std::vector<FillTask> &tasks, long long tickets, int K) {
+    const FillBufs b{&c->tasks, &c->prog, &c->cand, &c->ticket, &c->stage};
+    return run_fill_with(c, b, c->stream, cfg, mode, fold, tasks, tickets, K);
 }
 
 // Upload one or more scoring tables into c->scorings.
@@ -434,6 +446,7 @@ int sw_ctx_create(int device, void *cuda_stream, sw_ctx **out) {
     if (const char *f = std::getenv("SWGB_BATCH")) std::sscanf(f, "%d,%d,%d", &c->bat.R, &c->bat.W, &c->bat.P16);
     if (const char *f = std::getenv("SWGB_PROF32")) c->prof32 = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_ONE_ROUND")) c->one_round = std::atoi(f) != 0 ? 1 : 0;
+    if (const char *f = std::getenv("SWGB_LOOKAHEAD")) c->lookahead = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_TWO_LEVEL")) std::sscanf(f, "%lld,%lld", &c->two_level_bt1, &c->two_level_bt2);
     if (const char *f = std::getenv("SWGB_P16")) c->p16 = std::atoi(f) != 0;
     if (const char *f = std::getenv("SWGB_TB_BAND")) c->tb_band = std::atoi(f);
@@ -454,6 +467,12 @@ void sw_ctx_destroy(sw_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->side_go) cudaEventDestroy(c->side_go);
+    if (c->side_done) cudaEventDestroy(c->side_done);
     delete c;
 }
 

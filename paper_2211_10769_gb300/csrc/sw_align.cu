@@ -560,36 +560,44 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     const long long colck_ld = t.colck_ld, colaux_ld = t.colck_ld / aux_rows;
     long long CIc = -1, CJc = -1, R0c = 0, C0c = 0, Wi0 = m, Wj0 = n, ld2 = 0, N2 = 0;
     const int2 *rowck2 = nullptr, *colck2 = nullptr, *colaux2 = nullptr;
-    int prev_i = -1, prev_j = -1, prev_state = -1;
-    while (true) {
-        if (two && ((w.i - 1) / BT1 != CIc || (w.j - 1) / BT1 != CJc)) {
-            CIc = (w.i - 1) / BT1;
-            CJc = (w.j - 1) / BT1;
-            R0c = CIc * BT1; C0c = CJc * BT1;
-            Wi0 = w.i; Wj0 = w.j;
-            RC(refill_coarse_tile(c, da, db, n, ds, fwd, fold, aux_rows, rowck, colck, colaux, colck_ld, colaux_ld,
-                                  CIc, CJc, R0c, C0c, Wi0, Wj0, BT2, &rowck2, &colck2, &colaux2, &ld2, &N2));
-        }
-        const int I = (w.i - 1) / (int)BT, J = (w.j - 1) / (int)BT;
+
+    // A band: the tiles of tile rows I0..I along the diagonal through the cell (wi, wj), ending
+    // at that cell's tile row, in the buffers of slot s (0: the context's, 1: the look-ahead's).
+    // A tile depends only on the checkpoints, never on the walk, so a band may be recomputed
+    // ahead of the walk from a predicted cell; the walk stops at a tile missing from its table.
+    struct Band {
+        int slot = 0, I = 0, I0 = 0, nI = 0, nJ = 0, kd = 0;
+        int Itop = 0;                     // the band's top tile row with tiles (rows above it: cut by the cap)
+        std::vector<const void *> table;
+        std::vector<FillTask> tasks;
+        long long tickets = 0;
+    };
+    auto build_band = [&](long long wi, long long wj, int slot, Band &bd) {
+        bd = Band{};
+        bd.slot = slot;
+        char *tbp = static_cast<char *>(slot ? c->tb_b.p : c->tb.p);
+        int2 *bndp = static_cast<int2 *>(slot ? c->tbbnd_b.p : c->tbbnd.p);
+        const int I = (int)((wi - 1) / BT), J = (int)((wj - 1) / BT);
         const int It0 = (int)(R0c / BT), Jt0 = (int)(C0c / BT);       // the region's first tile row, column
         const int I0 = std::max(It0, I - band + 1);
         // the walk's table keeps kBandWidth tile columns a row along the diagonal: row ti holds
         // columns [ti + kd, ti + kd + kBandWidth), which contain every tile chosen below
         const int nI = I - I0 + 1, nJ = kBandWidth, kd = J - I - (kBandWidth - 2);
-        std::vector<const void *> table((size_t)nI * nJ, nullptr);
-        std::vector<FillTask> tasks;
-        long long tickets = 0;
-        // tiles of each tile row: the columns that the diagonal through the walk's cell crosses
-        // in that row, widened by BT / kBandMarginDiv on each side (two tiles a row, a third where the
+        bd.I = I; bd.I0 = I0; bd.nI = nI; bd.nJ = nJ; bd.kd = kd;
+        bd.table.assign((size_t)nI * nJ, nullptr);
+        // tiles of each tile row: the columns that the diagonal through the cell crosses in that
+        // row, widened by BT / kBandMarginDiv on each side (two tiles a row, a third where the
         // diagonal runs near a tile edge); a path that drifts further ends the round early
         const long long margin = BT / kBandMarginDiv;
+        int rows = 0;
         for (int d = 0; d < band && I - d >= It0; ++d) {
             const int ti = I - d;
             // one tile per SM at most (a second wave would double the round's time); whole rows
-            if (d > 0 && (int)tasks.size() + kBandWidth - 2 > c->nsm) break;
-            const long long rlo = (long long)ti * BT, rhi = std::min<long long>((long long)(ti + 1) * BT, w.i) - 1;
-            const long long clo = (long long)(w.j - 1) - ((long long)(w.i - 1) - rlo) - margin;
-            const long long chi = (long long)(w.j - 1) - ((long long)(w.i - 1) - rhi) + margin;
+            if (d > 0 && (int)bd.tasks.size() + kBandWidth - 2 > c->nsm) break;
+            ++rows;
+            const long long rlo = (long long)ti * BT, rhi = std::min<long long>((long long)(ti + 1) * BT, wi) - 1;
+            const long long clo = (wj - 1) - ((wi - 1) - rlo) - margin;
+            const long long chi = (wj - 1) - ((wi - 1) - rhi) + margin;
             const int wlo = ti + kd, whi = wlo + kBandWidth - 1;             // the table's window
             const int tlo = (int)std::min<long long>(J, std::max<long long>(std::max(Jt0, wlo), clo < 0 ? 0 : clo / BT));
             const int thi = (int)std::min<long long>(std::min(J, whi), std::max<long long>(tlo, chi < 0 ? 0 : chi / BT));
@@ -603,7 +611,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                 u.strip_warps = tsw;
                 u.nstrips = (u.rows + HS - 1) / HS;
                 u.scoring = 0;
-                u.ticket0 = tickets;
+                u.ticket0 = bd.tickets;
                 // the row above the tile and the column left of it: the matrix border, a
                 // forward-fill checkpoint (on a coarse boundary) or a refill checkpoint
                 if (r0 == 0) u.top = nullptr;
@@ -620,25 +628,92 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
                     u.left_aux = colaux2 + (size_t)((c0 - C0c) / BT - 1) * (ld2 / aux_rows) + (r0 - R0c) / aux_rows;
                     u.left_split = fwd.P16 ? 1 : 0;
                 }
-                const size_t k = tasks.size();
+                const size_t k = bd.tasks.size();
                 u.nslot = std::min(u.nstrips, 2);
-                u.bnd = static_cast<int2 *>(c->tbbnd.p) + k * 2 * (size_t)BT;
+                u.bnd = bndp + k * 2 * (size_t)BT;
                 u.ckpt_every = 0; u.ckpt = nullptr; u.colck = nullptr; u.colck_every = 0;
                 u.row0 = (int32_t)r0;
                 u.col0 = (int32_t)c0;
-                u.tb = static_cast<char *>(c->tb.p) + k * tile_bytes;
+                u.tb = tbp + k * tile_bytes;
                 u.tb_ld = BT;
-                tickets += u.nstrips;
-                tasks.push_back(u);
-                table[(size_t)(ti - I0) * nJ + (tj - (kd + I0) - (ti - I0))] = u.tb;
+                bd.tickets += u.nstrips;
+                bd.tasks.push_back(u);
+                bd.table[(size_t)(ti - I0) * nJ + (tj - (kd + I0) - (ti - I0))] = u.tb;
             }
         }
-        RC(run_fill(c, tbc, kModeTb, fold, tasks, tickets, ds.K));
-        const size_t tbytes = table.size() * sizeof(void *);
+        bd.Itop = I - rows + 1;
+    };
+    const FillBufs main_bufs{&c->tasks, &c->prog, &c->cand, &c->ticket, &c->stage};
+    const FillBufs side_bufs{&c->tasks_b, &c->prog_b, &c->cand_b, &c->ticket_b, &c->stage_b};
+    // the look-ahead band (one level only: a refill changes the checkpoints under the bands)
+    const bool ahead = c->lookahead && !two;
+    if (ahead) {
+        RC(c->tb_b.ensure(tile_bytes * maxtiles));
+        RC(c->tbbnd_b.ensure((size_t)maxtiles * 2 * (size_t)BT * sizeof(int2)));
+        RC(c->misc_b.ensure(table_cap * sizeof(void *)));
+        if (!c->side) CU(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        if (!c->side_go) CU(cudaEventCreateWithFlags(&c->side_go, cudaEventDisableTiming));
+        if (!c->side_done) CU(cudaEventCreateWithFlags(&c->side_done, cudaEventDisableTiming));
+    }
+    Band cur, spec;
+    bool have_spec = false;
+    // whatever happens below, the look-ahead fill is finished before this call returns
+    struct SideSync {
+        sw_ctx *c;
+        bool *on;
+        ~SideSync() { if (*on && c->side) cudaStreamSynchronize(c->side); }
+    } side_sync{c, &have_spec};
+    int prev_i = -1, prev_j = -1, prev_state = -1;
+    while (true) {
+        if (two && ((w.i - 1) / BT1 != CIc || (w.j - 1) / BT1 != CJc)) {
+            CIc = (w.i - 1) / BT1;
+            CJc = (w.j - 1) / BT1;
+            R0c = CIc * BT1; C0c = CJc * BT1;
+            Wi0 = w.i; Wj0 = w.j;
+            RC(refill_coarse_tile(c, da, db, n, ds, fwd, fold, aux_rows, rowck, colck, colaux, colck_ld, colaux_ld,
+                                  CIc, CJc, R0c, C0c, Wi0, Wj0, BT2, &rowck2, &colck2, &colaux2, &ld2, &N2));
+        }
+        const int Iw = (w.i - 1) / (int)BT, Jw = (w.j - 1) / (int)BT;
+        bool use_spec = false;
+        if (have_spec) {
+            // the look-ahead band serves if it holds the tile the walk is in
+            const int tj = Jw - (spec.kd + spec.I0) - (Iw - spec.I0);
+            use_spec = Iw <= spec.I && Iw >= spec.I0 && tj >= 0 && tj < spec.nJ &&
+                       spec.table[(size_t)(Iw - spec.I0) * spec.nJ + tj] != nullptr;
+            if (use_spec) {
+                CU(cudaStreamWaitEvent(c->stream, c->side_done, 0));
+                cur = std::move(spec);
+            } else {
+                CU(cudaStreamSynchronize(c->side));   // its buffers may be needed again
+            }
+            have_spec = false;
+        }
+        if (!use_spec) {
+            build_band(w.i, w.j, 0, cur);
+            RC(run_fill_with(c, main_bufs, c->stream, tbc, kModeTb, fold, cur.tasks, cur.tickets, ds.K));
+        }
+        const size_t tbytes = cur.table.size() * sizeof(void *);
         if (tbytes > c->stage2.cap) return SW_EINVAL;
-        std::memcpy(c->stage2.p, table.data(), tbytes);
-        CU(cudaMemcpyAsync(c->misc.p, c->stage2.p, tbytes, cudaMemcpyHostToDevice, c->stream));
-        RC(launch_walk(c, static_cast<const void *const *>(c->misc.p), I0, kd + I0, nI, nJ, (int)BT, R));
+        std::memcpy(c->stage2.p, cur.table.data(), tbytes);
+        void *dtab = cur.slot ? c->misc_b.p : c->misc.p;
+        CU(cudaMemcpyAsync(dtab, c->stage2.p, tbytes, cudaMemcpyHostToDevice, c->stream));
+        if (ahead) CU(cudaEventRecord(c->side_go, c->stream));   // the band's tiles are done
+        RC(launch_walk(c, static_cast<const void *const *>(dtab), cur.I0, cur.kd + cur.I0, cur.nI, cur.nJ,
+                       (int)BT, R));
+        // the next band up the same diagonal, recomputed on the side stream while the walk runs
+        if (ahead && cur.Itop > 0) {
+            const long long pi = (long long)cur.Itop * BT, pj = (long long)w.j - ((long long)w.i - pi);
+            if (pj >= 1) {
+                build_band(pi, pj, 1 - cur.slot, spec);
+                if (!spec.tasks.empty()) {
+                    CU(cudaStreamWaitEvent(c->side, c->side_go, 0));
+                    RC(run_fill_with(c, spec.slot ? side_bufs : main_bufs, c->side, tbc, kModeTb, fold, spec.tasks,
+                                     spec.tickets, ds.K));
+                    CU(cudaEventRecord(c->side_done, c->side));
+                    have_spec = true;
+                }
+            }
+        }
         CU(cudaMemcpyAsync(c->stage3.p, c->walk.p, sizeof(WalkState), cudaMemcpyDeviceToHost, c->stream));
         CU(cudaMemcpyAsync(static_cast<char *>(c->stage3.p) + 64, c->err.p, sizeof(int),
                            cudaMemcpyDeviceToHost, c->stream));
@@ -652,6 +727,10 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
         if (w.done != 0) break;
         if (w.i == prev_i && w.j == prev_j && w.state == prev_state) return SW_ECUDA;   // no progress
         prev_i = w.i; prev_j = w.j; prev_state = w.state;
+    }
+    if (have_spec) {
+        CU(cudaStreamSynchronize(c->side));
+        have_spec = false;
     }
     if (w.done != 1) return SW_ECUDA;     // the walk must end at a zero cell or the border
     if (w.nruns < 0 || (size_t)w.nruns * sizeof(int2) > runs_max) return SW_ECUDA;

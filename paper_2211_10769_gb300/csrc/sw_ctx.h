@@ -87,6 +87,13 @@ struct sw_ctx {
         ckpt2, colck2, colaux2,
         tbbnd, runs, walk, misc, dbscratch, dbslots, dbovf, dbjob, dbscores, topk;
     swgb::HostBuf stage, stage2, stage3;
+    // sw_align's look-ahead band: a second set of traceback-fill buffers and a stream of their
+    // own, so that the next band's tiles are recomputed while the walk goes through the current one
+    swgb::DevBuf tb_b, tbbnd_b, tasks_b, prog_b, cand_b, ticket_b, misc_b;
+    swgb::HostBuf stage_b;
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_go = nullptr, side_done = nullptr;
+    bool lookahead = true;
     std::vector<std::pair<long long, swgb::FillConfig>> batch_tune;   // autotuned tile shape per size class
     swgb::KernelTimer timer;
 };
@@ -114,6 +121,14 @@ int tb_word_bytes(int R);
 bool fold_open(const DevScoring &s);   // S + open fits the int8 profile
 int launch_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const FillLaunch &L, int K,
                 long long tickets);
+// the buffers a fill's launch uses: its task table, progress counters, candidates, ticket
+// counter and host staging (run_fill: the context's)
+struct FillBufs {
+    DevBuf *tasks, *prog, *cand, *ticket;
+    HostBuf *stage;
+};
+int run_fill_with(sw_ctx *c, const FillBufs &b, cudaStream_t st, const FillConfig &cfg, int mode, bool fold,
+                  const std::vector<FillTask> &tasks, long long tickets, int K);
 int run_fill(sw_ctx *c, const FillConfig &cfg, int mode, bool fold, const std::vector<FillTask> &tasks,
              long long tickets, int K);
 int upload_scorings(sw_ctx *c, const std::vector<DevScoring> &s);
