@@ -293,6 +293,34 @@ def test_align_paths_cross_tiles(ctx, oracle_mod, case):
     assert got.cigar == want.cigar
 
 
+@pytest.mark.parametrize("lookahead", ["0", "1"])
+def test_bands_with_and_without_lookahead(oracle_mod, monkeypatch, lookahead):
+    """The banded reconstruction with bands of two tile rows (many rounds),
+    with and without the look-ahead band recomputed while the walk runs:
+    a path along the diagonal (the look-ahead band serves) and paths with
+    long gaps that leave it (the look-ahead band is discarded)."""
+    from paper_2211_10769_gb300 import binding
+    monkeypatch.setenv("SWGB_ONE_ROUND", "0")
+    monkeypatch.setenv("SWGB_LOOKAHEAD", lookahead)
+    monkeypatch.setenv("SWGB_TB_BAND", "2")
+    c = binding.Context(0)
+    try:
+        seed = W.BASE_SEED + 9950
+        S2 = np.full((4, 4), -4, np.int8)
+        np.fill_diagonal(S2, 5)
+        A = W.uniform_dna(9000, seed)
+        cases = [(A, W.mutate(A, 4, seed + 1, p_sub=0.08, p_indel=0.01), W.dna_matrix(), 5, 2),
+                 (*_long_gap_pair(seed + 10, 8000, 2500, 4200, insert=False), S2, 20, 1),
+                 (*_long_gap_pair(seed + 20, 8000, 3000, 4400, insert=True), S2, 20, 1)]
+        for a, b, S, o, e in cases:
+            want = oracle_mod.sw_align_ptr(a, b, S, o, e)
+            got = c.align(a, b, S, o, e)
+            assert (got.score, got.a_begin, got.a_end, got.b_begin, got.b_end, got.cigar) == \
+                (want.score, want.a_begin, want.a_end, want.b_begin, want.b_end, want.cigar)
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("fwd", ["8,8,5", "8,8,6", "8,4,3", "16,4,1", "12,4", "4,4",
                                  "8,4,0,2,1", "12,4,0,2,1", "16,4,0,2,1", "12,4,2,2,1"])
 def test_strip_heights(oracle_mod, monkeypatch, fwd):
