@@ -215,23 +215,32 @@ int refill_coarse_tile(sw_ctx *c, const uint8_t *da, const uint8_t *db, int64_t 
 constexpr int64_t kOneRoundSide = 8192;
 
 // Tile side of a small pair's reconstruction: a multiple of both fills' strip
-// heights and of the chunk, at least kWalkMinBT; 0 if none fits.
-long long small_pair_tile(const sw_ctx *c, int64_t m, const DevScoring &ds, FillConfig *fwd_out, FillConfig *tbc_out,
-                          int *sw_out) {
+// heights and of the chunk, at least kWalkMinBT, the smallest whose tiles fit
+// one wave on the SMs (else the largest tried, up to the pair's side); 0 if
+// none fits the chunk.
+long long small_pair_tile(const sw_ctx *c, int64_t m, int64_t n, const DevScoring &ds, FillConfig *fwd_out,
+                          FillConfig *tbc_out, int *sw_out, int *tsw_out) {
     const FillConfig fwd = pair_fill_config_for(c, m, ds);
-    const int sw = pair_strip_warps(c, fwd, m);
+    // strips of two compute warps (at R = 4: 256 rows) in both fills, so that a tile can be one
+    // two-warp strip of 256 rows: a small pair's forward chain has as many warps either way, and
+    // a tile recomputes in about half the steps of a 512-row one
+    const int sw = c->fwd_auto ? std::min(2, fwd.W) : pair_strip_warps(c, fwd, m);
     const int HC = sw * 32 * fwd.R;
     // the traceback tiles continue the forward fill's staircase checkpoint columns lane by
     // lane, so both fills must give each lane the same rows (R)
     FillConfig tbc = (c->tbc.R == fwd.R && fwd.alg == kAlgLocal) ? c->tbc : FillConfig{fwd.R, 4};
     tbc.P16 = 0;
     tbc.alg = fwd.alg;
-    const long long BL = std::lcm((long long)HC, (long long)fill_rows_per_strip(tbc));
-    const long long BT = BL * ((kWalkMinBT + BL - 1) / BL);
+    const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : std::min(2, tbc.W);
+    const long long BL = std::lcm((long long)HC, (long long)tsw * 32 * tbc.R);
+    long long BT = BL * ((kWalkMinBT + BL - 1) / BL);
+    auto tiles = [&](long long bt) { return ((m + bt - 1) / bt) * ((n + bt - 1) / bt); };
+    while (tiles(BT) > c->nsm && BT < std::max(m, n)) BT += BL;
     if (BT % kCH != 0) return 0;
     *fwd_out = fwd;
     *tbc_out = tbc;
     *sw_out = sw;
+    *tsw_out = tsw;
     return BT;
 }
 
@@ -244,11 +253,11 @@ long long small_pair_tile(const sw_ctx *c, int64_t m, const DevScoring &ds, Fill
 // host round trip between the end cell and its band; for a pair whose tiles
 // fit one wave on the SMs, recomputing all of them costs no more time.
 int align_one_round(sw_ctx *c, const uint8_t *da, int64_t m, const uint8_t *db, int64_t n, const DevScoring &ds,
-                    bool fold, const FillConfig &fwd, const FillConfig &tbc, int sw, long long BT, sw_alignment *out) {
+                    bool fold, const FillConfig &fwd, const FillConfig &tbc, int sw, int tsw, long long BT,
+                    sw_alignment *out) {
     const int HC = sw * 32 * fwd.R;
     const int R = tbc.R;
     const int aux_rows = fwd.P16 ? fwd.R / 2 : fwd.R;
-    const int tsw = c->tb_strip_warps > 0 ? std::min(c->tb_strip_warps, tbc.W) : tbc.W;
     const int HS = tsw * 32 * R;
     if (BT % HC != 0 || BT % HS != 0) return SW_EINVAL;
     const int nI = (int)((m + BT - 1) / BT), nJ = (int)((n + BT - 1) / BT);
@@ -418,11 +427,11 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     if (c->one_round != 0 && std::max(m, n) <= kOneRoundSide) {
         // one round: forced (one_round > 0), or by default where every tile fits one wave on the SMs
         FillConfig f1{8, 4}, t1{8, 4};
-        int sw1 = 4;
-        const long long bt = small_pair_tile(c, m, ds, &f1, &t1, &sw1);
+        int sw1 = 4, tsw1 = 4;
+        const long long bt = small_pair_tile(c, m, n, ds, &f1, &t1, &sw1, &tsw1);
         const long long tiles = bt > 0 ? ((m + bt - 1) / bt) * ((n + bt - 1) / bt) : 0;
         if (bt > 0 && (c->one_round > 0 || tiles <= c->nsm))
-            return align_one_round(c, da, m, db, n, ds, fold, f1, t1, sw1, bt, out);
+            return align_one_round(c, da, m, db, n, ds, fold, f1, t1, sw1, tsw1, bt, out);
     }
 
     // ---- tile side: both checkpoint sets within the budget
@@ -453,7 +462,7 @@ extern "C" int sw_align(sw_ctx *c, const uint8_t *a, int64_t m, const uint8_t *b
     // path enters is filled again from them with fine checkpoints every BT2 (the other half)
     // pairs up to kSmallPairSide take tiles from 512 (a traceback tile is one strip of its
     // fill, half the chain of a 1,024 tile; 2 kbp: 0.22 -> ~0.11 ms of tile recompute)
-    const long long min_side = std::max(m, n) <= kSmallPairSide ? kWalkMinBT : 1024;
+    const long long min_side = std::max(m, n) <= kSmallPairSide ? 512 : 1024;
     long long BT1 = BL * ((min_side + BL - 1) / BL);
     while (ck_bytes(BT1) > c->ckpt_budget && BT1 < (1LL << 30)) BT1 *= 2;
     long long BT2 = BT1;

@@ -64,7 +64,7 @@ constexpr int kStageThreads = 256;    // threads staging a window (warps 1..8)
 constexpr int kWalkThreads = 32 + kStageThreads;   // warp 0 walks
 constexpr int kStage = 16;            // window words a thread loads at once
 constexpr int kWinMargin = 16;        // columns a staged window must leave either side of the walk's cell
-constexpr int kWalkMinBT = 512;       // tiles at least this side
+constexpr int kWalkMinBT = 256;       // tiles at least this side
 
 // Row groups of a window on tiles of side BT: its rows, and its band of
 // columns ((groups - 1) R + kWinCols wide), each within BT, so that a window
